@@ -1,0 +1,246 @@
+/*
+ * CPU oracle for guided (banded, Z-drop) extension alignment.
+ *
+ * TEST INFRASTRUCTURE ONLY.  Only the tests, the smoke check and the CPU
+ * baseline leg of the benchmark load this file.  It shares no code, header or
+ * constant with the CUDA library: it is a plain, slow restatement of what the
+ * method computes, written so a reader can check it against the paper by eye.
+ *
+ * What is computed (paper Section 2.1):
+ *   - Eq. 1-3: affine-gap dynamic programming over the score table of a
+ *     reference (target) T and a query Q, H(i,j) = max(E, F, H(i-1,j-1)+S).
+ *     Extended to two-piece affine gaps: a gap of length l costs
+ *     min(q + l*e, q2 + l*e2), so two extra gap states E2/F2 run with (q2, e2).
+ *     The paper's alpha/beta (open/extend) map to q+e and e.
+ *   - "Guiding strategy": only the band |t - q| <= w is computed (k-banding).
+ *   - Eq. 4-7: exact termination (Z-drop).  For every anti-diagonal c in
+ *     order, take its maximum H (lowest t on ties).  If it beats the global
+ *     maximum the global maximum moves there; otherwise, if it lies below and
+ *     to the right of the global maximum and the drop exceeds
+ *     Z + e2*|(i-i')-(j-j')|, the extension stops.
+ * Readings where the paper is silent (boundary, tie-breaks, outputs) follow the
+ * minimap2 extension convention and are listed in the design notes.
+ *
+ * Arithmetic is int64 with a sentinel far below any reachable score, so no
+ * wrap-around can occur; only the outputs use -2^30 as "not reached".
+ */
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+#include <pthread.h>
+
+#define ORC_OUT_NEG_INF (-0x40000000)
+#define ORC_MINUS_INF (INT64_MIN / 4)
+
+typedef struct {
+    int32_t a, b, q, e, q2, e2, w, zdrop, end_bonus;
+} orc_params;
+
+typedef struct {
+    int32_t max, qe, te, gscore, mqe, mqe_t, mte, mte_q;
+    int64_t cells;
+    uint8_t zdropped, reach_end, pad[6];
+} orc_result;
+
+static int64_t imax64(int64_t x, int64_t y) { return x > y ? x : y; }
+static int64_t imin64(int64_t x, int64_t y) { return x < y ? x : y; }
+
+/* Cost of one gap of length l >= 1 under the two-piece model. */
+static int64_t gap_cost(const orc_params *p, int64_t l)
+{
+    return imin64((int64_t)p->q + l * p->e, (int64_t)p->q2 + l * p->e2);
+}
+
+/* A real cell (t, q) of the table that lies inside the band. */
+static int in_band(int64_t t, int64_t q, int64_t tlen, int64_t qlen, int64_t w)
+{
+    if (t < 0 || q < 0 || t >= tlen || q >= qlen) return 0;
+    int64_t k = t - q;
+    return k <= w && -k <= w;
+}
+
+/* One cell's state: H and the four gap states ending at that cell. */
+typedef struct { int64_t H, E, F, E2, F2; } cell_state;
+
+/*
+ * Align one pair.  T (length tlen) is the reference, Q (length qlen) the
+ * query, both as codes 0..3.  Parameters must already be normalised
+ * (see orc_normalise).
+ */
+void orc_align_pair(const uint8_t *T, int32_t tlen, const uint8_t *Q, int32_t qlen,
+                    const orc_params *p_in, orc_result *out)
+{
+    orc_params p = *p_in;
+    memset(out, 0, sizeof(*out));
+    out->max = 0; out->qe = -1; out->te = -1;
+    out->gscore = ORC_OUT_NEG_INF; out->mqe = ORC_OUT_NEG_INF; out->mte = ORC_OUT_NEG_INF;
+    out->mqe_t = -1; out->mte_q = -1;
+    if (tlen <= 0 || qlen <= 0) return;
+
+    int64_t w = p.w;
+    if (w < 0 || w > (int64_t)(tlen > qlen ? tlen : qlen)) w = tlen > qlen ? tlen : qlen;
+
+    /* prev1[t]: cells of anti-diagonal r-1, prev2[t]: r-2, cur[t]: r.  Index t. */
+    cell_state *prev2 = (cell_state *)malloc(sizeof(cell_state) * (size_t)tlen);
+    cell_state *prev1 = (cell_state *)malloc(sizeof(cell_state) * (size_t)tlen);
+    cell_state *cur = (cell_state *)malloc(sizeof(cell_state) * (size_t)tlen);
+    if (!prev2 || !prev1 || !cur) { free(prev2); free(prev1); free(cur); out->zdropped = 255; return; }
+
+    int64_t gmax = 0, gmax_t = -1, gmax_q = -1;   /* the origin (-1,-1), score 0 */
+    int64_t mqe = ORC_MINUS_INF, mqe_t = -1, mte = ORC_MINUS_INF, mte_q = -1;
+    int64_t gscore = ORC_MINUS_INF;
+    int64_t cells = 0;
+    int zdropped = 0;
+    const int64_t last_r = (int64_t)tlen + qlen - 2;
+
+    for (int64_t r = 0; r <= last_r; ++r) {
+        /* band cells of anti-diagonal r: t in [st, en] */
+        int64_t st = 0, en = tlen - 1;
+        if (r - qlen + 1 > st) st = r - qlen + 1;
+        int64_t lo = r - w;                              /* t >= ceil((r-w)/2) */
+        int64_t lo2 = lo >= 0 ? (lo + 1) / 2 : -((-lo) / 2);
+        if (lo2 > st) st = lo2;
+        if (r < en) en = r;
+        int64_t hi = r + w;                              /* t <= floor((r+w)/2) */
+        int64_t hi2 = hi >= 0 ? hi / 2 : -((-hi + 1) / 2);
+        if (hi2 < en) en = hi2;
+        if (st > en) { zdropped = 1; break; }           /* the band left the table */
+
+        int64_t m = ORC_MINUS_INF, m_t = -1;
+        for (int64_t t = st; t <= en; ++t) {
+            int64_t q = r - t;
+            /* diagonal predecessor H(t-1, q-1) */
+            int64_t Hdiag;
+            if (t == 0 && q == 0) Hdiag = 0;
+            else if (t == 0) Hdiag = -gap_cost(&p, q);          /* H(-1, q-1) */
+            else if (q == 0) Hdiag = -gap_cost(&p, t);          /* H(t-1, -1) */
+            else Hdiag = prev2[t - 1].H;                        /* same diagonal: in band */
+            /* upper predecessor (t-1, q): opens/extends E and E2 */
+            int64_t Hup, Eup, E2up;
+            if (t == 0) { Hup = -gap_cost(&p, q + 1); Eup = ORC_MINUS_INF; E2up = ORC_MINUS_INF; }
+            else if (in_band(t - 1, q, tlen, qlen, w)) { Hup = prev1[t - 1].H; Eup = prev1[t - 1].E; E2up = prev1[t - 1].E2; }
+            else { Hup = ORC_MINUS_INF; Eup = ORC_MINUS_INF; E2up = ORC_MINUS_INF; }
+            /* left predecessor (t, q-1): opens/extends F and F2 */
+            int64_t Hleft, Fleft, F2left;
+            if (q == 0) { Hleft = -gap_cost(&p, t + 1); Fleft = ORC_MINUS_INF; F2left = ORC_MINUS_INF; }
+            else if (in_band(t, q - 1, tlen, qlen, w)) { Hleft = prev1[t].H; Fleft = prev1[t].F; F2left = prev1[t].F2; }
+            else { Hleft = ORC_MINUS_INF; Fleft = ORC_MINUS_INF; F2left = ORC_MINUS_INF; }
+
+            int64_t E = imax64(Hup - p.q - p.e, Eup - p.e);
+            int64_t E2 = imax64(Hup - p.q2 - p.e2, E2up - p.e2);
+            int64_t F = imax64(Hleft - p.q - p.e, Fleft - p.e);
+            int64_t F2 = imax64(Hleft - p.q2 - p.e2, F2left - p.e2);
+            int64_t s = (T[t] == Q[q]) ? p.a : -(int64_t)p.b;
+            int64_t H = Hdiag + s;
+            H = imax64(H, E); H = imax64(H, F); H = imax64(H, E2); H = imax64(H, F2);
+            cur[t].H = H; cur[t].E = E; cur[t].F = F; cur[t].E2 = E2; cur[t].F2 = F2;
+            if (H > m) { m = H; m_t = t; }                  /* lowest t on ties */
+        }
+        cells += en - st + 1;
+
+        /* best score reaching the last target base / the last query base */
+        if (en == tlen - 1 && r - (tlen - 1) >= 0 && r - (tlen - 1) < qlen) {
+            int64_t H = cur[tlen - 1].H;
+            if (H > mte) { mte = H; mte_q = r - (tlen - 1); }
+        }
+        {
+            int64_t tq = r - (qlen - 1);
+            if (tq >= st && tq <= en) {
+                int64_t H = cur[tq].H;
+                if (H > mqe) { mqe = H; mqe_t = tq; }
+            }
+        }
+        /* Eq. 4-7: global max update, else the Z-drop test */
+        int64_t m_q = r - m_t;
+        if (m > gmax) {
+            gmax = m; gmax_t = m_t; gmax_q = m_q;
+        } else if (m_t >= gmax_t && m_q >= gmax_q && p.zdrop >= 0) {
+            int64_t dt = m_t - gmax_t, dq = m_q - gmax_q;
+            int64_t l = dt > dq ? dt - dq : dq - dt;
+            if (gmax - m > (int64_t)p.zdrop + l * p.e2) { zdropped = 1; break; }
+        }
+        if (r == last_r && en == tlen - 1) gscore = cur[tlen - 1].H;
+
+        cell_state *tmp = prev2; prev2 = prev1; prev1 = cur; cur = tmp;
+    }
+
+    out->max = (int32_t)gmax; out->te = (int32_t)gmax_t; out->qe = (int32_t)gmax_q;
+    out->gscore = gscore == ORC_MINUS_INF ? ORC_OUT_NEG_INF : (int32_t)gscore;
+    out->mqe = mqe == ORC_MINUS_INF ? ORC_OUT_NEG_INF : (int32_t)mqe;
+    out->mte = mte == ORC_MINUS_INF ? ORC_OUT_NEG_INF : (int32_t)mte;
+    out->mqe_t = (int32_t)mqe_t; out->mte_q = (int32_t)mte_q;
+    out->cells = cells;
+    out->zdropped = (uint8_t)zdropped;
+    out->reach_end = (uint8_t)(!zdropped && mqe != ORC_MINUS_INF &&
+                               mqe + p.end_bonus > gmax);
+    free(prev2); free(prev1); free(cur);
+}
+
+/*
+ * Two-piece parameters that cannot help collapse to one piece: with
+ * q2 <= q or e2 >= e the second piece is never the cheaper one for long gaps
+ * and the model is the single-piece one, (q2, e2) = (q, e).
+ */
+void orc_normalise(orc_params *p)
+{
+    if (p->q2 <= p->q || p->e2 >= p->e) { p->q2 = p->q; p->e2 = p->e; }
+}
+
+/* ----------------------------------------------------------------------- */
+/* Batch driver: pairs spread over threads, longest first, for timing only. */
+
+typedef struct {
+    const uint8_t *q_codes, *t_codes;
+    const int64_t *q_off, *t_off;
+    const int32_t *q_len, *t_len;
+    const int64_t *order;
+    int64_t n;
+    orc_params p;
+    orc_result *out;
+    int64_t next;
+    pthread_mutex_t lock;
+} orc_job;
+
+static void *orc_worker(void *arg)
+{
+    orc_job *job = (orc_job *)arg;
+    for (;;) {
+        pthread_mutex_lock(&job->lock);
+        int64_t k = job->next;
+        job->next += 1;
+        pthread_mutex_unlock(&job->lock);
+        if (k >= job->n) break;
+        int64_t i = job->order ? job->order[k] : k;
+        orc_align_pair(job->t_codes + job->t_off[i], job->t_len[i],
+                       job->q_codes + job->q_off[i], job->q_len[i], &job->p, &job->out[i]);
+    }
+    return NULL;
+}
+
+/* Align n pairs with n_threads threads; order (may be NULL) is the schedule. */
+int orc_align_batch(const uint8_t *q_codes, const uint8_t *t_codes,
+                    const int64_t *q_off, const int64_t *t_off,
+                    const int32_t *q_len, const int32_t *t_len,
+                    const int64_t *order, int64_t n, const orc_params *p,
+                    orc_result *out, int n_threads)
+{
+    orc_job job;
+    job.q_codes = q_codes; job.t_codes = t_codes; job.q_off = q_off; job.t_off = t_off;
+    job.q_len = q_len; job.t_len = t_len; job.order = order; job.n = n;
+    job.p = *p; orc_normalise(&job.p);
+    job.out = out; job.next = 0;
+    pthread_mutex_init(&job.lock, NULL);
+    if (n_threads < 1) n_threads = 1;
+    pthread_t *th = (pthread_t *)malloc(sizeof(pthread_t) * (size_t)n_threads);
+    if (!th) return -1;
+    int started = 0;
+    for (int i = 0; i < n_threads; ++i)
+        if (pthread_create(&th[i], NULL, orc_worker, &job) == 0) ++started;
+    if (started == 0) orc_worker(&job);
+    for (int i = 0; i < started; ++i) pthread_join(th[i], NULL);
+    free(th);
+    pthread_mutex_destroy(&job.lock);
+    return 0;
+}
+
+int orc_result_size(void) { return (int)sizeof(orc_result); }
