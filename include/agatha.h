@@ -1,0 +1,226 @@
+/*
+ * agatha.h - C ABI of a GB300 (sm_103a) library for guided extension
+ * alignment: banded, two-piece affine, score-only dynamic programming with the
+ * exact Z-drop termination rule, batched over many read/reference pairs.
+ *
+ * The operation (AGAThA, PPoPP'24, arxiv 2403.06478):
+ *   - Section 2.1, Eq. 1-3: for a reference (target) T and a query Q the score
+ *     table H(t,q) = max(H(t-1,q-1) + S(T[t],Q[q]), E(t,q), F(t,q)) with affine
+ *     gap states E (steps in t) and F (steps in q).  Here the gaps are
+ *     two-piece affine: a gap of length l costs min(q + l*e, q2 + l*e2), so two
+ *     more states E2, F2 run with (q2, e2).  Match scores +a, mismatch -b.
+ *   - Section 2.1 "Guiding Strategy": only cells with |t - q| <= w are computed.
+ *   - Section 2.1, Eq. 4-7: anti-diagonals r = t + q are visited in order; the
+ *     maximum of each (lowest t on ties) either becomes the new global maximum
+ *     (strictly greater) or, if it lies at t >= max_t and q >= max_q, ends the
+ *     extension when max - H > zdrop + e2 * |(t - max_t) - (q - max_q)|.
+ *   - An anti-diagonal with no band cell (|tlen - qlen| > w) also ends the
+ *     extension with zdropped = 1.
+ *   - Virtual row/column: H(-1,-1) = 0, H(-1,q) = -gap(q+1), H(t,-1) =
+ *     -gap(t+1); they are not band-restricted.  Only real cells are banded.
+ *
+ * Conventions used by every entry point:
+ *   - Return value: AGATHA_OK (0) or a negative AGATHA_E* code.  No C++
+ *     exception crosses this boundary.  agatha_strerror() names a code and
+ *     agatha_last_error() gives the context's last detailed message.
+ *   - Ownership: the caller owns every buffer it passes.  The library never
+ *     keeps a pointer to caller memory after a call returns (after the stream
+ *     work completes, with AGATHA_ASYNC).
+ *   - Sequences: 2-bit codes A=0, C=1, G=2, T=3, 16 bases per uint32 word;
+ *     base k of a packed stream sits at bits 2*(k%16)..2*(k%16)+1 of word k/16.
+ *     N is not representable: agatha_pack_ascii rejects it with AGATHA_EINVAL.
+ *   - NEG_INF (-2^30) in a result means "not reached".
+ */
+#ifndef AGATHA_H
+#define AGATHA_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define AGATHA_NEG_INF (-0x40000000)
+
+/* Error codes. */
+#define AGATHA_OK          0
+#define AGATHA_EINVAL     -1   /* bad parameter, offset or length            */
+#define AGATHA_ENOMEM     -2   /* device or host allocation failed / budget   */
+#define AGATHA_ECUDA      -3   /* a CUDA runtime call failed                  */
+#define AGATHA_ETIMEDOUT  -4   /* serve wait ran out of time                  */
+#define AGATHA_EAGAIN     -5   /* serve ticket still pending                  */
+#define AGATHA_ECANCELED  -6   /* request cancelled by agatha_serve_stop      */
+#define AGATHA_EDEVICE    -7   /* the device reported an error status         */
+#define AGATHA_ENOTSUP    -8   /* configuration not supported                 */
+
+/* Flags for agatha_align_batch. */
+#define AGATHA_HOST_PTRS   0x00u  /* batch arrays and `out` are host memory  */
+#define AGATHA_DEVICE_PTRS 0x01u  /* batch arrays and `out` are device memory*/
+#define AGATHA_PLAIN       0x02u  /* plain kernel: one pair per block, input
+                                     order, one launch (the comparison path) */
+#define AGATHA_ASYNC       0x04u  /* DEVICE_PTRS only: return once enqueued   */
+#define AGATHA_NO_SORT     0x08u  /* batched kernel in input order (no LPT)   */
+#define AGATHA_FORCE32     0x10u  /* never use 16-bit packed lanes            */
+#define AGATHA_NO_GRAPH    0x20u  /* launch directly, no CUDA graph replay    */
+#define AGATHA_EDGE_PATH_ONLY 0x40u /* batched kernel: run every anti-diagonal
+                                     through the masked edge path (testing)  */
+
+typedef struct agatha_ctx agatha_ctx;
+
+/* Scoring and guiding parameters (minimap2 naming).
+ *   a >= 0 match score, b >= 0 mismatch penalty, q/e gap open/extend (piece 1),
+ *   q2/e2 (piece 2); all penalties >= 0.  If q2 <= q or e2 >= e the model is
+ *   single-piece (q2 = q, e2 = e), as the second piece can then never be the
+ *   cheaper one for long gaps.  w != 0 is the band half-width (w < 0: no band);
+ *   zdrop < 0 disables Z-drop; end_bonus only affects reach_end. */
+typedef struct {
+    int32_t a, b, q, e, q2, e2, w, zdrop, end_bonus;
+} agatha_params;
+
+/* A batch of pairs.  Pair i is Q = q_packed bases [q_off[i], q_off[i]+q_len[i])
+ * and T = t_packed bases [t_off[i], t_off[i]+t_len[i]).  q_words/t_words give
+ * the size of each packed stream in uint32 words; every sequence must lie
+ * inside its stream (EINVAL otherwise).  Lengths >= 0 and < 2^24. */
+typedef struct {
+    int64_t n_pairs;
+    const uint32_t *q_packed;
+    const uint32_t *t_packed;
+    int64_t q_words;
+    int64_t t_words;
+    const int64_t *q_off;
+    const int64_t *t_off;
+    const int32_t *q_len;
+    const int32_t *t_len;
+} agatha_batch;
+
+/* Per-pair result (48 bytes).
+ *   max, te, qe   : global maximum and its cell (target end, query end);
+ *                   max = 0, te = qe = -1 when nothing beats the origin.
+ *   gscore        : H(tlen-1, qlen-1) if the last anti-diagonal was reached
+ *                   and that cell is in band, else NEG_INF.
+ *   mqe, mqe_t    : best H on the last query column (q = qlen-1), its t.
+ *   mte, mte_q    : best H on the last target row (t = tlen-1), its q.
+ *   cells         : band cells of all anti-diagonals processed, up to and
+ *                   including the one where the extension stopped.
+ *   zdropped      : 1 if Z-drop (or the band leaving the table) stopped it.
+ *   reach_end     : !zdropped && mqe + end_bonus > max.
+ *   lane16        : 1 if the pair ran on 16-bit packed lanes. */
+typedef struct {
+    int32_t max, qe, te, gscore, mqe, mqe_t, mte, mte_q;
+    int64_t cells;
+    uint8_t zdropped, reach_end, lane16, pad[5];
+} agatha_result;
+
+/* Context configuration.  device: CUDA ordinal.  mem_budget_bytes: device
+ * memory the context may hold for batch buffers (0: no limit).  max_pairs:
+ * hint for the first allocation (0: grow on demand).  tune_cache_path: file
+ * where the autotuner keeps its choices (NULL: in memory only). */
+typedef struct {
+    int32_t device;
+    int32_t flags;
+    int64_t mem_budget_bytes;
+    int64_t max_pairs;
+    const char *tune_cache_path;
+} agatha_config;
+
+/* Create a context on cfg->device (cfg may be NULL: device 0, defaults).
+ * Allocates the context's stream and small control buffers.  Errors:
+ * EINVAL (ctx NULL, bad device), ECUDA, ENOMEM. */
+int agatha_init(agatha_ctx **ctx, const agatha_config *cfg);
+
+/* Release every resource of the context (stops serving first).  NULL is a
+ * no-op. */
+void agatha_destroy(agatha_ctx *ctx);
+
+/* Align every pair of `batch` with `params` and write out[0..n_pairs).
+ *   flags: AGATHA_HOST_PTRS (default) - batch arrays and out in host memory;
+ *          the library copies them to the device on `stream` and copies the
+ *          results back before returning.
+ *          AGATHA_DEVICE_PTRS - all arrays are device pointers on ctx's device;
+ *          with AGATHA_ASYNC the call returns after enqueueing on `stream`.
+ *          AGATHA_PLAIN selects the plain one-pair-per-block kernel;
+ *          otherwise the batched persistent kernel runs (work queue ordered by
+ *          predicted band cells, longest first, CUDA graph replay).
+ *   stream: cudaStream_t to run on (NULL: the context's own stream).
+ * Errors: EINVAL (bad params: w == 0, a negative score or penalty, lengths or
+ * offsets outside the streams; checked before any kernel runs for host
+ * batches, and by a device check before the alignment for device batches),
+ * ENOMEM, ECUDA, EDEVICE. */
+int agatha_align_batch(agatha_ctx *ctx, const agatha_batch *batch,
+                       const agatha_params *params, agatha_result *out,
+                       uint32_t flags, void *stream);
+
+/* Check parameters on the host without touching the GPU: AGATHA_OK or
+ * AGATHA_EINVAL.  `normalised` (may be NULL) receives the parameters the
+ * kernels use (two-piece collapsed when the second piece never helps). */
+int agatha_check_params(const agatha_params *params, agatha_params *normalised);
+
+/* Pack n bases given as codes 0..3 into 16-base words.  out must hold
+ * (n + 15) / 16 words; unused high bits of the last word are zero.
+ * EINVAL if a code is > 3 or n < 0. */
+int agatha_pack_codes(const uint8_t *codes, int64_t n, uint32_t *out);
+
+/* Same from ASCII A/C/G/T (either case).  EINVAL on any other byte (N too). */
+int agatha_pack_ascii(const char *ascii, int64_t n, uint32_t *out);
+
+/* Band cells of the whole table of a tlen x qlen pair with half-width w
+ * (w < 0: unbanded): the work estimate used for scheduling. */
+int64_t agatha_band_cells(int32_t tlen, int32_t qlen, int32_t w);
+
+/* ---------------------------------------------------------------------- */
+/* Serving: continuous batching of alignment requests on one device.       */
+
+typedef struct {
+    int64_t mem_budget_bytes;   /* device bytes admitted requests may hold */
+    int32_t max_inflight;       /* requests on the device at once (>= 1)   */
+    int32_t max_batch_pairs;    /* pairs merged into one device launch     */
+    int32_t linger_us;          /* wait this long for more requests        */
+    int32_t pad;
+} agatha_serve_config;
+
+typedef struct {
+    int64_t requests_done, pairs_done, cells_done;
+    int64_t launches;
+    int64_t bytes_in_flight, peak_bytes_in_flight;
+    double busy_seconds;        /* wall time with work on the device        */
+    double p50_latency_ms, p99_latency_ms;
+} agatha_serve_stats;
+
+/* Start the scheduler thread of ctx (one server per context).  EINVAL on a
+ * bad config, EAGAIN if already serving. */
+int agatha_serve_start(agatha_ctx *ctx, const agatha_serve_config *cfg);
+
+/* Submit a request (host pointers; copied before return).  `out` (host,
+ * n_pairs results) must stay valid until the ticket completes.  ENOMEM if the
+ * request alone exceeds the memory budget; EINVAL on a bad batch. */
+int agatha_serve_submit(agatha_ctx *ctx, const agatha_batch *batch,
+                        const agatha_params *params, agatha_result *out,
+                        uint64_t *ticket);
+
+/* AGATHA_OK if the ticket is complete (results written), AGATHA_EAGAIN if
+ * pending, AGATHA_ECANCELED if cancelled, EINVAL for an unknown ticket. */
+int agatha_serve_poll(agatha_ctx *ctx, uint64_t ticket);
+
+/* Wait up to timeout_ms (< 0: forever).  OK, ETIMEDOUT, ECANCELED, EINVAL.
+ * A completed ticket is forgotten after a successful wait. */
+int agatha_serve_wait(agatha_ctx *ctx, uint64_t ticket, int32_t timeout_ms);
+
+/* Snapshot of the server's counters. */
+int agatha_serve_stats_get(agatha_ctx *ctx, agatha_serve_stats *stats);
+
+/* Stop the scheduler.  drain != 0: finish every admitted and queued request;
+ * drain == 0: finish requests already on the device, cancel queued ones. */
+int agatha_serve_stop(agatha_ctx *ctx, int32_t drain);
+
+/* ---------------------------------------------------------------------- */
+
+const char *agatha_strerror(int code);
+const char *agatha_last_error(agatha_ctx *ctx);
+/* Library version (major*10000 + minor*100 + patch). */
+int32_t agatha_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* AGATHA_H */

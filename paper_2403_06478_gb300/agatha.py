@@ -1,0 +1,306 @@
+"""Python binding of ``libagatha.so`` (ctypes).  Argument marshalling only.
+
+Every name mirrors the C ABI in ``include/agatha.h``: ``agatha_init``,
+``agatha_align_batch``, ``agatha_pack_codes`` ...  The alignment itself runs
+in the library's CUDA kernels; this module never computes a score.  If the
+library is missing the import of a function fails loudly; there is no
+fallback of any kind.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from dataclasses import dataclass
+from typing import Optional, Sequence
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libagatha.so")
+
+AGATHA_OK = 0
+AGATHA_EINVAL = -1
+AGATHA_ENOMEM = -2
+AGATHA_ECUDA = -3
+AGATHA_ETIMEDOUT = -4
+AGATHA_EAGAIN = -5
+AGATHA_ECANCELED = -6
+AGATHA_EDEVICE = -7
+AGATHA_ENOTSUP = -8
+
+AGATHA_HOST_PTRS = 0x00
+AGATHA_DEVICE_PTRS = 0x01
+AGATHA_PLAIN = 0x02
+AGATHA_ASYNC = 0x04
+AGATHA_NO_SORT = 0x08
+AGATHA_FORCE32 = 0x10
+AGATHA_NO_GRAPH = 0x20
+AGATHA_EDGE_PATH_ONLY = 0x40
+
+NEG_INF = -0x40000000
+
+RESULT_DTYPE = np.dtype([
+    ("max", np.int32), ("qe", np.int32), ("te", np.int32), ("gscore", np.int32),
+    ("mqe", np.int32), ("mqe_t", np.int32), ("mte", np.int32), ("mte_q", np.int32),
+    ("cells", np.int64), ("zdropped", np.uint8), ("reach_end", np.uint8),
+    ("lane16", np.uint8), ("pad", np.uint8, (5,)),
+])
+assert RESULT_DTYPE.itemsize == 48
+
+RESULT_FIELDS = ("max", "qe", "te", "gscore", "mqe", "mqe_t", "mte", "mte_q", "cells",
+                 "zdropped", "reach_end")
+
+
+class AgathaError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"{msg} (code {code})")
+        self.code = code
+
+
+class agatha_params(ctypes.Structure):
+    _fields_ = [(n, ctypes.c_int32) for n in
+                ("a", "b", "q", "e", "q2", "e2", "w", "zdrop", "end_bonus")]
+
+
+class agatha_batch(ctypes.Structure):
+    _fields_ = [("n_pairs", ctypes.c_int64),
+                ("q_packed", ctypes.c_void_p), ("t_packed", ctypes.c_void_p),
+                ("q_words", ctypes.c_int64), ("t_words", ctypes.c_int64),
+                ("q_off", ctypes.c_void_p), ("t_off", ctypes.c_void_p),
+                ("q_len", ctypes.c_void_p), ("t_len", ctypes.c_void_p)]
+
+
+class agatha_config(ctypes.Structure):
+    _fields_ = [("device", ctypes.c_int32), ("flags", ctypes.c_int32),
+                ("mem_budget_bytes", ctypes.c_int64), ("max_pairs", ctypes.c_int64),
+                ("tune_cache_path", ctypes.c_char_p)]
+
+
+class agatha_serve_config(ctypes.Structure):
+    _fields_ = [("mem_budget_bytes", ctypes.c_int64), ("max_inflight", ctypes.c_int32),
+                ("max_batch_pairs", ctypes.c_int32), ("linger_us", ctypes.c_int32),
+                ("pad", ctypes.c_int32)]
+
+
+class agatha_serve_stats(ctypes.Structure):
+    _fields_ = [("requests_done", ctypes.c_int64), ("pairs_done", ctypes.c_int64),
+                ("cells_done", ctypes.c_int64), ("launches", ctypes.c_int64),
+                ("bytes_in_flight", ctypes.c_int64), ("peak_bytes_in_flight", ctypes.c_int64),
+                ("busy_seconds", ctypes.c_double), ("p50_latency_ms", ctypes.c_double),
+                ("p99_latency_ms", ctypes.c_double)]
+
+
+_lib = None
+
+# every function the header declares, with its ctypes signature
+_SIGS = {
+    "agatha_init": (ctypes.c_int, [ctypes.POINTER(ctypes.c_void_p), ctypes.POINTER(agatha_config)]),
+    "agatha_destroy": (None, [ctypes.c_void_p]),
+    "agatha_align_batch": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(agatha_batch),
+                                          ctypes.POINTER(agatha_params), ctypes.c_void_p,
+                                          ctypes.c_uint32, ctypes.c_void_p]),
+    "agatha_check_params": (ctypes.c_int, [ctypes.POINTER(agatha_params), ctypes.POINTER(agatha_params)]),
+    "agatha_pack_codes": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p]),
+    "agatha_pack_ascii": (ctypes.c_int, [ctypes.c_char_p, ctypes.c_int64, ctypes.c_void_p]),
+    "agatha_band_cells": (ctypes.c_int64, [ctypes.c_int32, ctypes.c_int32, ctypes.c_int32]),
+    "agatha_serve_start": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(agatha_serve_config)]),
+    "agatha_serve_submit": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(agatha_batch),
+                                           ctypes.POINTER(agatha_params), ctypes.c_void_p,
+                                           ctypes.POINTER(ctypes.c_uint64)]),
+    "agatha_serve_poll": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_uint64]),
+    "agatha_serve_wait": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_uint64, ctypes.c_int32]),
+    "agatha_serve_stats_get": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(agatha_serve_stats)]),
+    "agatha_serve_stop": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32]),
+    "agatha_strerror": (ctypes.c_char_p, [ctypes.c_int]),
+    "agatha_last_error": (ctypes.c_char_p, [ctypes.c_void_p]),
+    "agatha_version": (ctypes.c_int32, []),
+}
+
+
+def lib():
+    """The loaded library; raises if it has not been built."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise ImportError(f"{LIB_PATH} is missing: run __graft_entry__.build() "
+                              "(or python -m paper_2403_06478_gb300.build) first")
+        L = ctypes.CDLL(LIB_PATH)
+        for name, (res, args) in _SIGS.items():
+            fn = getattr(L, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = L
+    return _lib
+
+
+def declared_symbols():
+    return tuple(_SIGS)
+
+
+def _check(code: int, ctx=None, what: str = "agatha"):
+    if code != AGATHA_OK:
+        msg = lib().agatha_strerror(code).decode()
+        if ctx is not None:
+            detail = lib().agatha_last_error(ctx)
+            if detail:
+                msg += ": " + detail.decode()
+        raise AgathaError(code, f"{what}: {msg}")
+
+
+def make_params(scoring) -> agatha_params:
+    t = scoring.as_tuple() if hasattr(scoring, "as_tuple") else tuple(scoring)
+    return agatha_params(*[int(x) for x in t])
+
+
+def agatha_check_params(scoring) -> agatha_params:
+    out = agatha_params()
+    _check(lib().agatha_check_params(ctypes.byref(make_params(scoring)), ctypes.byref(out)))
+    return out
+
+
+def agatha_band_cells(tlen: int, qlen: int, w: int) -> int:
+    return int(lib().agatha_band_cells(int(tlen), int(qlen), int(w)))
+
+
+def agatha_pack_codes(codes: np.ndarray) -> np.ndarray:
+    """Pack codes 0..3 into 16-base uint32 words (runs in the library)."""
+    codes = np.ascontiguousarray(codes, dtype=np.uint8)
+    n = int(codes.shape[0])
+    out = np.zeros(max(1, (n + 15) // 16), dtype=np.uint32)
+    _check(lib().agatha_pack_codes(codes.ctypes.data if n else None, n, out.ctypes.data),
+           what="agatha_pack_codes")
+    return out
+
+
+def agatha_pack_ascii(s: bytes) -> np.ndarray:
+    n = len(s)
+    out = np.zeros(max(1, (n + 15) // 16), dtype=np.uint32)
+    _check(lib().agatha_pack_ascii(s, n, out.ctypes.data), what="agatha_pack_ascii")
+    return out
+
+
+@dataclass
+class PackedBatch:
+    """Host arrays of a batch in the library's input format."""
+    q_packed: np.ndarray
+    t_packed: np.ndarray
+    q_off: np.ndarray
+    t_off: np.ndarray
+    q_len: np.ndarray
+    t_len: np.ndarray
+
+    @property
+    def n_pairs(self) -> int:
+        return int(self.q_len.shape[0])
+
+    def nbytes(self) -> int:
+        return sum(int(a.nbytes) for a in (self.q_packed, self.t_packed, self.q_off,
+                                             self.t_off, self.q_len, self.t_len))
+
+
+def pack_batch(batch) -> PackedBatch:
+    """Pack a workload batch (concatenated codes) with the library's packer."""
+    return PackedBatch(agatha_pack_codes(batch.q_codes), agatha_pack_codes(batch.t_codes),
+                       np.ascontiguousarray(batch.q_off, dtype=np.int64),
+                       np.ascontiguousarray(batch.t_off, dtype=np.int64),
+                       np.ascontiguousarray(batch.q_len, dtype=np.int32),
+                       np.ascontiguousarray(batch.t_len, dtype=np.int32))
+
+
+def _host_batch(pb: PackedBatch) -> agatha_batch:
+    return agatha_batch(pb.n_pairs, pb.q_packed.ctypes.data, pb.t_packed.ctypes.data,
+                        int(pb.q_packed.shape[0]), int(pb.t_packed.shape[0]),
+                        pb.q_off.ctypes.data, pb.t_off.ctypes.data,
+                        pb.q_len.ctypes.data, pb.t_len.ctypes.data)
+
+
+class Context:
+    """An ``agatha_ctx`` on one device."""
+
+    def __init__(self, device: int = 0, mem_budget_bytes: int = 0, max_pairs: int = 0,
+                 tune_cache_path: Optional[str] = None):
+        self._ptr = ctypes.c_void_p()
+        cfg = agatha_config(device, 0, mem_budget_bytes, max_pairs,
+                            tune_cache_path.encode() if tune_cache_path else None)
+        _check(lib().agatha_init(ctypes.byref(self._ptr), ctypes.byref(cfg)), what="agatha_init")
+
+    @property
+    def handle(self):
+        return self._ptr
+
+    def close(self):
+        if self._ptr:
+            lib().agatha_destroy(self._ptr)
+            self._ptr = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def last_error(self) -> str:
+        return lib().agatha_last_error(self._ptr).decode()
+
+    # -- alignment ---------------------------------------------------------
+    def align_host(self, pb: PackedBatch, scoring, flags: int = 0, stream: int = 0,
+                   out: Optional[np.ndarray] = None) -> np.ndarray:
+        """agatha_align_batch with host arrays; returns the result records."""
+        n = pb.n_pairs
+        if out is None:
+            out = np.zeros(n, dtype=RESULT_DTYPE)
+        b = _host_batch(pb)
+        p = make_params(scoring)
+        rc = lib().agatha_align_batch(self._ptr, ctypes.byref(b), ctypes.byref(p),
+                                      out.ctypes.data if n else None,
+                                      ctypes.c_uint32(flags & ~AGATHA_DEVICE_PTRS),
+                                      ctypes.c_void_p(stream) if stream else None)
+        _check(rc, self._ptr, "agatha_align_batch")
+        return out
+
+    def align_device(self, q_packed, t_packed, q_off, t_off, q_len, t_len, out, scoring,
+                     flags: int = 0, stream: int = 0) -> None:
+        """agatha_align_batch on device tensors (torch CUDA tensors or raw pointers).
+
+        ``out`` is a uint8 device tensor of n_pairs * 48 bytes."""
+        def ptr(x):
+            return int(x.data_ptr()) if hasattr(x, "data_ptr") else int(x)
+
+        def numel(x):
+            return int(x.numel()) if hasattr(x, "numel") else int(len(x))
+
+        n = numel(q_len)
+        b = agatha_batch(n, ptr(q_packed), ptr(t_packed), numel(q_packed), numel(t_packed),
+                         ptr(q_off), ptr(t_off), ptr(q_len), ptr(t_len))
+        p = make_params(scoring)
+        rc = lib().agatha_align_batch(self._ptr, ctypes.byref(b), ctypes.byref(p),
+                                      ctypes.c_void_p(ptr(out)),
+                                      ctypes.c_uint32(flags | AGATHA_DEVICE_PTRS),
+                                      ctypes.c_void_p(stream) if stream else None)
+        _check(rc, self._ptr, "agatha_align_batch")
+
+
+def agatha_init(device: int = 0, **kw) -> Context:
+    return Context(device, **kw)
+
+
+def agatha_align_batch(ctx: Context, batch, scoring=None, flags: int = 0, stream: int = 0):
+    """Align a workload batch (or a PackedBatch) on the GPU; host in, host out."""
+    pb = batch if isinstance(batch, PackedBatch) else pack_batch(batch)
+    if scoring is None:
+        scoring = batch.scoring
+    return ctx.align_host(pb, scoring, flags=flags, stream=stream)
+
+
+def results_equal(a: np.ndarray, b: np.ndarray, fields: Sequence[str] = RESULT_FIELDS):
+    """Indices of records that differ in any compared field."""
+    bad = np.zeros(a.shape[0], dtype=bool)
+    for f in fields:
+        bad |= a[f] != b[f]
+    return np.flatnonzero(bad)

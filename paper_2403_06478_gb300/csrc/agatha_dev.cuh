@@ -1,0 +1,155 @@
+// Device-side definitions shared by the alignment kernels of this library.
+//
+// Coordinates: t indexes the target (reference), q the query, r = t + q is the
+// anti-diagonal (paper Section 2.1: cells of one anti-diagonal are
+// independent).  Inside the band |t - q| <= w, anti-diagonal r holds the cells
+//     t in [ceil((r - w) / 2), floor((r + w) / 2)]
+// (clipped to the table).  The kernels index them by a "slot"
+//     j = t - B(r),   B(r) = ceil((r - w) / 2),   j in [0, w]
+// On anti-diagonals with (r - w) even all w+1 slots are band cells; when it is
+// odd slot w is outside the band (t - q = w + 1).  Going from r-1 to r:
+//   diagonal predecessor (t-1, q-1) sits in the same slot j on r-2,
+//   (t-1, q) [E, E2 input] sits in slot j-1 on r-1 if (r-w) is even, else j,
+//   (t, q-1) [F, F2 input] sits in slot j   on r-1 if (r-w) is even, else j+1.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "agatha.h"
+
+namespace agatha {
+
+// "Minus infinity" of the int32 kernels.  Scores are validated on the host to
+// stay within +-2^28, so this value is never reached by a real cell and
+// subtracting a few penalties from it cannot wrap.
+constexpr int32_t K_NEG = -(1 << 29);
+constexpr int32_t K_NEG_OUT = AGATHA_NEG_INF;
+
+struct DevParams {
+    int32_t a, b, q, e, q2, e2, w, zdrop, end_bonus;
+};
+
+// Batch descriptor, resident in device memory so that one captured CUDA graph
+// can be replayed for any batch the host stages.
+struct DevBatch {
+    const uint32_t *q_packed;
+    const uint32_t *t_packed;
+    int64_t q_words;
+    int64_t t_words;
+    const int64_t *q_off;
+    const int64_t *t_off;
+    const int32_t *q_len;
+    const int32_t *t_len;
+    agatha_result *out;
+    int64_t n_pairs;
+    // schedule produced by the prep kernels
+    int32_t *order;          // pair indices, longest predicted work first
+    int32_t *counters;       // [0] queue head of the batched kernel, [1] count of
+                             // pairs routed to the batched kernel, [2] wide pairs,
+                             // [3] error word
+    int32_t *wide_order;     // pairs whose band is too wide for the warp kernel
+    int64_t *bucket_hist;    // scratch for the ordering
+    DevParams params;
+    int32_t warp_w_max;      // widest band the warp kernel takes (32*C - 1)
+    int32_t pad;
+};
+
+enum : int32_t { CTR_HEAD = 0, CTR_NWARP = 1, CTR_NWIDE = 2, CTR_ERR = 3, CTR_WIDE_HEAD = 4,
+                 CTR_COUNT = 8 };
+
+// device error codes written to counters[CTR_ERR]
+enum : int32_t { DEV_ERR_NONE = 0, DEV_ERR_BAD_PAIR = 1 };
+
+__host__ __device__ inline int32_t floor_div2(int32_t x) { return x >> 1; }   // arithmetic shift
+__host__ __device__ inline int32_t ceil_div2(int32_t x) { return -((-x) >> 1); }
+
+__device__ __forceinline__ int32_t gap_cost(const DevParams &p, int32_t l) {
+    return min(p.q + l * p.e, p.q2 + l * p.e2);
+}
+
+// Effective half-width: a band wider than the table changes nothing.
+__host__ __device__ inline int32_t effective_w(int32_t w, int32_t tlen, int32_t qlen) {
+    int32_t m = tlen > qlen ? tlen : qlen;
+    return (w < 0 || w > m) ? m : w;
+}
+
+// One packed word of a stream, zero outside it (reads are clamped).
+__device__ __forceinline__ uint32_t load_word(const uint32_t *__restrict__ p, int64_t n_words,
+                                              int64_t i) {
+    return (i >= 0 && i < n_words) ? __ldg(p + i) : 0u;
+}
+
+// 16 consecutive bases starting at base index g (any g, outside reads give 0).
+__device__ __forceinline__ uint32_t load16(const uint32_t *__restrict__ p, int64_t n_words,
+                                           int64_t g) {
+    int64_t wi = g >> 4;                         // floor for negative g too
+    uint32_t sh = (uint32_t)(g & 15) * 2u;
+    uint32_t lo = load_word(p, n_words, wi);
+    uint32_t hi = load_word(p, n_words, wi + 1);
+    return __funnelshift_r(lo, hi, sh);
+}
+
+// 32 consecutive bases starting at g.
+__device__ __forceinline__ uint64_t load32(const uint32_t *__restrict__ p, int64_t n_words,
+                                           int64_t g) {
+    uint64_t lo = load16(p, n_words, g);
+    uint64_t hi = load16(p, n_words, g + 16);
+    return lo | (hi << 32);
+}
+
+// Reverse the order of the 2-bit fields of a word.
+__device__ __forceinline__ uint32_t rev2_32(uint32_t x) {
+    x = __brev(x);
+    return ((x >> 1) & 0x55555555u) | ((x & 0x55555555u) << 1);
+}
+__device__ __forceinline__ uint64_t rev2_64(uint64_t x) {
+    x = __brevll(x);
+    return ((x >> 1) & 0x5555555555555555ull) | ((x & 0x5555555555555555ull) << 1);
+}
+
+__device__ __forceinline__ void write_empty_result(agatha_result *o) {
+    agatha_result r;
+    r.max = 0; r.qe = -1; r.te = -1;
+    r.gscore = K_NEG_OUT; r.mqe = K_NEG_OUT; r.mte = K_NEG_OUT;
+    r.mqe_t = -1; r.mte_q = -1;
+    r.cells = 0;
+    r.zdropped = 0; r.reach_end = 0; r.lane16 = 0;
+    for (int i = 0; i < 5; ++i) r.pad[i] = 0;
+    *o = r;
+}
+
+// Band cells of anti-diagonal r (0 when empty).
+__device__ __forceinline__ int32_t band_cells_on(int32_t r, int32_t tlen, int32_t qlen, int32_t w) {
+    int32_t st = max(max(0, r - qlen + 1), ceil_div2(r - w));
+    int32_t en = min(min(tlen - 1, r), floor_div2(r + w));
+    return en >= st ? en - st + 1 : 0;
+}
+
+// A pair the kernels may align: lengths and offsets inside the streams, and
+// scores that keep int32 headroom.
+__device__ __forceinline__ bool pair_valid(const DevBatch &B, int64_t i) {
+    const int32_t tl = B.t_len[i], ql = B.q_len[i];
+    const int64_t to = B.t_off[i], qo = B.q_off[i];
+    if (tl < 0 || ql < 0 || tl >= (1 << 24) || ql >= (1 << 24)) return false;
+    if (to < 0 || qo < 0) return false;
+    if (to + tl > B.t_words * 16 || qo + ql > B.q_words * 16) return false;
+    const DevParams &p = B.params;
+    const int64_t unit = (int64_t)p.a + p.b + p.q + p.e + p.q2 + p.e2 + (p.end_bonus > 0 ? p.end_bonus : 0);
+    if (unit * ((int64_t)tl + ql + 2) >= (int64_t)1 << 28) return false;   // int32 headroom
+    return true;
+}
+
+// Launchers (defined in the .cu files).
+cudaError_t launch_prep(const DevBatch *d_batch, int64_t n_pairs, int32_t sort, cudaStream_t s,
+                        int n_sm);
+template <int C>
+cudaError_t launch_warp_c(const DevBatch *d_batch, int n_blocks, cudaStream_t s, int use_fast);
+template <int C>
+int occupancy_warp_c();
+cudaError_t launch_plain_kernel(const DevBatch *d_batch, int64_t n_blocks, int32_t w_max,
+                                int use_wide_list, cudaStream_t s);
+int plain_kernel_max_w();
+cudaError_t plain_kernel_prepare();
+
+}  // namespace agatha

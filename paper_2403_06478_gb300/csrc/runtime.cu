@@ -1,0 +1,534 @@
+// Host runtime behind the C ABI: context, device buffers, batch validation,
+// kernel selection, CUDA-graph replay and result copy-back.
+#include <algorithm>
+#include <atomic>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <mutex>
+#include <string>
+#include <thread>
+#include <tuple>
+#include <vector>
+
+#include "agatha_dev.cuh"
+#include "runtime.h"
+
+using namespace agatha;
+
+// ------------------------------------------------------------------ errors
+
+const char *agatha_strerror(int code) {
+    switch (code) {
+        case AGATHA_OK: return "ok";
+        case AGATHA_EINVAL: return "invalid argument";
+        case AGATHA_ENOMEM: return "out of memory or over budget";
+        case AGATHA_ECUDA: return "CUDA runtime error";
+        case AGATHA_ETIMEDOUT: return "timed out";
+        case AGATHA_EAGAIN: return "not ready";
+        case AGATHA_ECANCELED: return "cancelled";
+        case AGATHA_EDEVICE: return "device reported an error";
+        case AGATHA_ENOTSUP: return "not supported";
+        default: return "unknown error";
+    }
+}
+
+int32_t agatha_version(void) { return 100; }
+
+namespace agatha {
+
+int set_error(agatha_ctx *ctx, int code, const char *fmt, ...) {
+    if (ctx) {
+        char buf[512];
+        va_list ap;
+        va_start(ap, fmt);
+        vsnprintf(buf, sizeof(buf), fmt, ap);
+        va_end(ap);
+        std::lock_guard<std::mutex> g(ctx->err_mu);
+        ctx->last_error = buf;
+    }
+    return code;
+}
+
+int cuda_fail(agatha_ctx *ctx, cudaError_t e, const char *what) {
+    return set_error(ctx, AGATHA_ECUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+int DevBuf::ensure(agatha_ctx *ctx, size_t need) {
+    if (need <= cap) return AGATHA_OK;
+    size_t want = std::max(need, cap + cap / 2);
+    want = (want + 255) & ~(size_t)255;
+    const int64_t delta = (int64_t)want - (int64_t)cap;
+    if (ctx->mem_budget > 0 && ctx->mem_held + delta > ctx->mem_budget) {
+        want = need;
+        if (ctx->mem_held + ((int64_t)want - (int64_t)cap) > ctx->mem_budget)
+            return set_error(ctx, AGATHA_ENOMEM, "device buffer of %zu bytes exceeds the budget", need);
+    }
+    if (ptr) {
+        cudaStreamSynchronize(ctx->stream);
+        cudaFree(ptr);
+        ctx->mem_held -= (int64_t)cap;
+        ptr = nullptr;
+        cap = 0;
+    }
+    if (ctx->fail_alloc_after >= 0 && ctx->fail_alloc_after-- == 0)
+        return set_error(ctx, AGATHA_ENOMEM, "injected allocation failure");
+    cudaError_t e = cudaMalloc(&ptr, want);
+    if (e != cudaSuccess) {
+        ptr = nullptr;
+        cudaGetLastError();
+        return set_error(ctx, AGATHA_ENOMEM, "cudaMalloc(%zu): %s", want, cudaGetErrorString(e));
+    }
+    cap = want;
+    ctx->mem_held += (int64_t)want;
+    ctx->graphs_stale = true;     // graphs may bake buffer addresses
+    return AGATHA_OK;
+}
+
+void DevBuf::release() {
+    if (ptr) cudaFree(ptr);
+    ptr = nullptr;
+    cap = 0;
+}
+
+// ------------------------------------------------------------- parameters
+
+int normalise_params(const agatha_params *in, DevParams *out) {
+    if (!in) return AGATHA_EINVAL;
+    if (in->a < 0 || in->b < 0 || in->q < 0 || in->e < 0 || in->q2 < 0 || in->e2 < 0)
+        return AGATHA_EINVAL;
+    if (in->w == 0) return AGATHA_EINVAL;
+    if (in->a > (1 << 16) || in->b > (1 << 16) || in->q > (1 << 20) || in->e > (1 << 16) ||
+        in->q2 > (1 << 20) || in->e2 > (1 << 16) || in->end_bonus > (1 << 20) ||
+        in->end_bonus < -(1 << 20) || in->zdrop > (1 << 27))
+        return AGATHA_EINVAL;
+    DevParams p;
+    p.a = in->a; p.b = in->b; p.q = in->q; p.e = in->e; p.q2 = in->q2; p.e2 = in->e2;
+    p.w = in->w < 0 ? -1 : in->w;
+    p.zdrop = in->zdrop; p.end_bonus = in->end_bonus;
+    if (p.q2 <= p.q || p.e2 >= p.e) { p.q2 = p.q; p.e2 = p.e; }
+    *out = p;
+    return AGATHA_OK;
+}
+
+static int64_t score_unit(const DevParams &p) {
+    return (int64_t)p.a + p.b + p.q + p.e + p.q2 + p.e2 + (p.end_bonus > 0 ? p.end_bonus : 0);
+}
+
+// Host-side check of a host batch; fills the widest effective band.
+int validate_host_batch(agatha_ctx *ctx, const agatha_batch *b, const DevParams &p,
+                        BatchShape *shape) {
+    if (!b || b->n_pairs < 0 || b->n_pairs > (int64_t)INT32_MAX - 1)
+        return set_error(ctx, AGATHA_EINVAL, "bad batch or n_pairs");
+    shape->n = b->n_pairs;
+    shape->max_w_warp = 0;
+    shape->max_w_all = 0;
+    shape->max_len = 0;
+    if (b->n_pairs == 0) return AGATHA_OK;
+    if (!b->q_len || !b->t_len || !b->q_off || !b->t_off)
+        return set_error(ctx, AGATHA_EINVAL, "null batch array");
+    if (b->q_words < 0 || b->t_words < 0) return set_error(ctx, AGATHA_EINVAL, "negative stream size");
+    if ((b->q_words > 0 && !b->q_packed) || (b->t_words > 0 && !b->t_packed))
+        return set_error(ctx, AGATHA_EINVAL, "null packed stream");
+    const int64_t unit = score_unit(p);
+    for (int64_t i = 0; i < b->n_pairs; ++i) {
+        const int32_t tl = b->t_len[i], ql = b->q_len[i];
+        const int64_t to = b->t_off[i], qo = b->q_off[i];
+        if (tl < 0 || ql < 0 || tl >= (1 << 24) || ql >= (1 << 24))
+            return set_error(ctx, AGATHA_EINVAL, "pair %lld: bad length", (long long)i);
+        if (to < 0 || qo < 0 || to + tl > b->t_words * 16 || qo + ql > b->q_words * 16)
+            return set_error(ctx, AGATHA_EINVAL, "pair %lld: sequence outside its stream", (long long)i);
+        if (unit * ((int64_t)tl + ql + 2) >= ((int64_t)1 << 28))
+            return set_error(ctx, AGATHA_EINVAL, "pair %lld: scores could overflow int32", (long long)i);
+        shape->max_len = std::max<int64_t>(shape->max_len, std::max(tl, ql));
+        if (tl > 0 && ql > 0)
+            shape->max_w_all = std::max(shape->max_w_all, effective_w(p.w, tl, ql));
+    }
+    return AGATHA_OK;
+}
+
+int pick_slots_per_lane(int32_t w) {
+    const int cs[] = {4, 8, 16, 24, 32};
+    for (int c : cs)
+        if (32 * c - 1 >= w) return c;
+    return 32;
+}
+
+static cudaError_t launch_warp(int C, const DevBatch *d, int blocks, cudaStream_t s, int fast) {
+    switch (C) {
+        case 4: return launch_warp_c<4>(d, blocks, s, fast);
+        case 8: return launch_warp_c<8>(d, blocks, s, fast);
+        case 16: return launch_warp_c<16>(d, blocks, s, fast);
+        case 24: return launch_warp_c<24>(d, blocks, s, fast);
+        default: return launch_warp_c<32>(d, blocks, s, fast);
+    }
+}
+
+int warp_occupancy(int C) {
+    switch (C) {
+        case 4: return occupancy_warp_c<4>();
+        case 8: return occupancy_warp_c<8>();
+        case 16: return occupancy_warp_c<16>();
+        case 24: return occupancy_warp_c<24>();
+        default: return occupancy_warp_c<32>();
+    }
+}
+
+// Enqueue the device work of one batch whose descriptor is already on the
+// device.  Captured into a CUDA graph unless the caller asked otherwise.
+static cudaError_t enqueue_batch(agatha_ctx *ctx, const LaunchPlan &lp, cudaStream_t s) {
+    cudaError_t e = cudaMemsetAsync(ctx->counters.ptr, 0, CTR_COUNT * sizeof(int32_t), s);
+    if (e != cudaSuccess) return e;
+    if (lp.plain) {
+        // validation only (no sort), then the plain kernel over every pair
+        e = launch_prep(ctx->d_desc, lp.n, 0, s, ctx->n_sm);
+        if (e != cudaSuccess) return e;
+        return launch_plain_kernel(ctx->d_desc, lp.plain_blocks, lp.plain_w, 0, s);
+    }
+    e = cudaMemsetAsync(ctx->hist.ptr, 0, 256 * sizeof(int64_t), s);
+    if (e != cudaSuccess) return e;
+    e = launch_prep(ctx->d_desc, lp.n, lp.sort, s, ctx->n_sm);
+    if (e != cudaSuccess) return e;
+    e = launch_warp(lp.C, ctx->d_desc, lp.warp_blocks, s, lp.fast);
+    if (e != cudaSuccess) return e;
+    if (lp.wide_w > 0) e = launch_plain_kernel(ctx->d_desc, (int64_t)ctx->n_sm * 2, lp.wide_w, 1, s);
+    return e;
+}
+
+static cudaError_t run_plan(agatha_ctx *ctx, const LaunchPlan &lp, cudaStream_t s) {
+    if (!lp.use_graph) return enqueue_batch(ctx, lp, s);
+    if (ctx->graphs_stale) {
+        for (auto &kv : ctx->graphs) cudaGraphExecDestroy(kv.second);
+        ctx->graphs.clear();
+        ctx->graphs_stale = false;
+    }
+    const auto key = lp.key();
+    auto it = ctx->graphs.find(key);
+    if (it == ctx->graphs.end()) {
+        cudaGraph_t g = nullptr;
+        cudaError_t e = cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal);
+        if (e != cudaSuccess) return e;
+        cudaError_t e1 = enqueue_batch(ctx, lp, s);
+        e = cudaStreamEndCapture(s, &g);
+        if (e1 != cudaSuccess) { if (g) cudaGraphDestroy(g); return e1; }
+        if (e != cudaSuccess) return e;
+        cudaGraphExec_t ge = nullptr;
+        e = cudaGraphInstantiate(&ge, g, 0);
+        cudaGraphDestroy(g);
+        if (e != cudaSuccess) return e;
+        it = ctx->graphs.emplace(key, ge).first;
+    }
+    return cudaGraphLaunch(it->second, s);
+}
+
+int ensure_batch_buffers(agatha_ctx *ctx, int64_t n, int64_t q_words, int64_t t_words,
+                         bool copy_inputs) {
+    int rc;
+    const int64_t n1 = std::max<int64_t>(n, 1);
+    if (copy_inputs) {
+        if ((rc = ctx->q_packed.ensure(ctx, (size_t)std::max<int64_t>(q_words, 1) * 4))) return rc;
+        if ((rc = ctx->t_packed.ensure(ctx, (size_t)std::max<int64_t>(t_words, 1) * 4))) return rc;
+        if ((rc = ctx->q_off.ensure(ctx, (size_t)n1 * 8))) return rc;
+        if ((rc = ctx->t_off.ensure(ctx, (size_t)n1 * 8))) return rc;
+        if ((rc = ctx->q_len.ensure(ctx, (size_t)n1 * 4))) return rc;
+        if ((rc = ctx->t_len.ensure(ctx, (size_t)n1 * 4))) return rc;
+        if ((rc = ctx->out.ensure(ctx, (size_t)n1 * sizeof(agatha_result)))) return rc;
+    }
+    if ((rc = ctx->order.ensure(ctx, (size_t)n1 * 4))) return rc;
+    if ((rc = ctx->wide_order.ensure(ctx, (size_t)n1 * 4))) return rc;
+    return AGATHA_OK;
+}
+
+// Build the launch plan of a batch: which kernels, grids and graph key.
+int make_plan(agatha_ctx *ctx, const DevParams &p, const BatchShape &shape, uint32_t flags,
+              LaunchPlan *lp) {
+    lp->n = shape.n;
+    lp->plain = (flags & AGATHA_PLAIN) != 0;
+    lp->sort = (flags & AGATHA_NO_SORT) ? 0 : 1;
+    lp->fast = (flags & AGATHA_EDGE_PATH_ONLY) ? 0 : 1;
+    lp->use_graph = (flags & (AGATHA_NO_GRAPH | AGATHA_PLAIN)) ? 0 : 1;
+    const int32_t pmax = plain_kernel_max_w();
+    if (lp->plain) {
+        lp->C = 0;
+        lp->plain_w = std::max<int32_t>(shape.max_w_all, 1);
+        if (lp->plain_w > pmax)
+            return set_error(ctx, AGATHA_ENOTSUP, "band of %d cells is wider than the plain kernel's %d",
+                             lp->plain_w, pmax);
+        lp->plain_blocks = std::max<int64_t>(shape.n, 1);
+        lp->warp_blocks = 0;
+        lp->wide_w = 0;
+        lp->warp_w_max = 0;
+        return AGATHA_OK;
+    }
+    lp->C = pick_slots_per_lane(shape.max_w_all);
+    lp->warp_w_max = 32 * lp->C - 1;
+    lp->wide_w = shape.max_w_all > lp->warp_w_max ? shape.max_w_all : 0;
+    if (lp->wide_w > pmax)
+        return set_error(ctx, AGATHA_ENOTSUP, "band of %d cells is wider than supported (%d)",
+                         lp->wide_w, pmax);
+    const int occ = warp_occupancy(lp->C);
+    lp->warp_blocks = ctx->n_sm * occ;
+    lp->plain_w = 0;
+    lp->plain_blocks = 0;
+    return AGATHA_OK;
+}
+
+void fill_desc(agatha_ctx *ctx, DevBatch *d, const DevParams &p, const LaunchPlan &lp) {
+    d->order = (lp.sort && !lp.plain) ? (int32_t *)ctx->order.ptr : nullptr;
+    d->counters = (int32_t *)ctx->counters.ptr;
+    d->wide_order = (int32_t *)ctx->wide_order.ptr;
+    d->bucket_hist = (int64_t *)ctx->hist.ptr;
+    d->params = p;
+    d->warp_w_max = lp.plain ? INT32_MAX : lp.warp_w_max;
+    d->pad = 0;
+}
+
+}  // namespace agatha
+
+// ------------------------------------------------------------------ ABI
+
+extern "C" int agatha_check_params(const agatha_params *params, agatha_params *normalised) {
+    DevParams p;
+    int rc = normalise_params(params, &p);
+    if (rc) return rc;
+    if (normalised) {
+        normalised->a = p.a; normalised->b = p.b; normalised->q = p.q; normalised->e = p.e;
+        normalised->q2 = p.q2; normalised->e2 = p.e2; normalised->w = p.w;
+        normalised->zdrop = p.zdrop; normalised->end_bonus = p.end_bonus;
+    }
+    return AGATHA_OK;
+}
+
+extern "C" int agatha_init(agatha_ctx **out, const agatha_config *cfg) {
+    if (!out) return AGATHA_EINVAL;
+    *out = nullptr;
+    agatha_config c;
+    std::memset(&c, 0, sizeof(c));
+    if (cfg) c = *cfg;
+    int ndev = 0;
+    cudaError_t e = cudaGetDeviceCount(&ndev);
+    if (e != cudaSuccess) { cudaGetLastError(); return AGATHA_ECUDA; }
+    if (c.device < 0 || c.device >= ndev) return AGATHA_EINVAL;
+    agatha_ctx *ctx = new (std::nothrow) agatha_ctx();
+    if (!ctx) return AGATHA_ENOMEM;
+    ctx->device = c.device;
+    ctx->mem_budget = c.mem_budget_bytes;
+    if (c.tune_cache_path) ctx->tune_cache_path = c.tune_cache_path;
+    if ((e = cudaSetDevice(c.device)) != cudaSuccess) { delete ctx; return AGATHA_ECUDA; }
+    cudaDeviceProp prop;
+    if ((e = cudaGetDeviceProperties(&prop, c.device)) != cudaSuccess) { delete ctx; return AGATHA_ECUDA; }
+    ctx->n_sm = prop.multiProcessorCount;
+    ctx->cc_major = prop.major;
+    ctx->cc_minor = prop.minor;
+    if ((e = cudaStreamCreateWithFlags(&ctx->stream, cudaStreamNonBlocking)) != cudaSuccess) {
+        delete ctx;
+        return AGATHA_ECUDA;
+    }
+    int rc;
+    if ((rc = ctx->counters.ensure(ctx, CTR_COUNT * sizeof(int32_t))) ||
+        (rc = ctx->hist.ensure(ctx, 256 * sizeof(int64_t))) ||
+        (rc = ctx->desc.ensure(ctx, sizeof(DevBatch)))) {
+        agatha_destroy(ctx);
+        return rc;
+    }
+    ctx->d_desc = (DevBatch *)ctx->desc.ptr;
+    if (cudaMallocHost(&ctx->h_desc, sizeof(DevBatch)) != cudaSuccess ||
+        cudaMallocHost(&ctx->h_counters, CTR_COUNT * sizeof(int32_t)) != cudaSuccess) {
+        cudaGetLastError();
+        agatha_destroy(ctx);
+        return AGATHA_ENOMEM;
+    }
+    if ((e = plain_kernel_prepare()) != cudaSuccess) {
+        agatha_destroy(ctx);
+        return AGATHA_ECUDA;
+    }
+    if (c.max_pairs > 0) ensure_batch_buffers(ctx, c.max_pairs, 0, 0, true);
+    *out = ctx;
+    return AGATHA_OK;
+}
+
+extern "C" void agatha_destroy(agatha_ctx *ctx) {
+    if (!ctx) return;
+    agatha_serve_stop(ctx, 0);
+    cudaSetDevice(ctx->device);
+    if (ctx->stream) cudaStreamSynchronize(ctx->stream);
+    for (auto &kv : ctx->graphs) cudaGraphExecDestroy(kv.second);
+    ctx->graphs.clear();
+    DevBuf *bufs[] = {&ctx->q_packed, &ctx->t_packed, &ctx->q_off, &ctx->t_off, &ctx->q_len,
+                      &ctx->t_len, &ctx->out, &ctx->order, &ctx->wide_order, &ctx->counters,
+                      &ctx->hist, &ctx->desc};
+    for (DevBuf *b : bufs) b->release();
+    if (ctx->h_desc) cudaFreeHost(ctx->h_desc);
+    if (ctx->h_counters) cudaFreeHost(ctx->h_counters);
+    if (ctx->stream) cudaStreamDestroy(ctx->stream);
+    delete ctx;
+}
+
+extern "C" const char *agatha_last_error(agatha_ctx *ctx) {
+    if (!ctx) return "no context";
+    std::lock_guard<std::mutex> g(ctx->err_mu);
+    ctx->last_error_copy = ctx->last_error;
+    return ctx->last_error_copy.c_str();
+}
+
+extern "C" int agatha_align_batch(agatha_ctx *ctx, const agatha_batch *batch,
+                                  const agatha_params *params, agatha_result *out, uint32_t flags,
+                                  void *stream) {
+    if (!ctx || !batch || !params) return AGATHA_EINVAL;
+    std::lock_guard<std::mutex> lock(ctx->mu);
+    DevParams p;
+    if (normalise_params(params, &p)) return set_error(ctx, AGATHA_EINVAL, "bad scoring parameters");
+    if (batch->n_pairs < 0) return set_error(ctx, AGATHA_EINVAL, "negative n_pairs");
+    if (batch->n_pairs > 0 && !out) return set_error(ctx, AGATHA_EINVAL, "null out");
+    const bool dev = (flags & AGATHA_DEVICE_PTRS) != 0;
+    if ((flags & AGATHA_ASYNC) && !dev) return set_error(ctx, AGATHA_EINVAL, "ASYNC needs DEVICE_PTRS");
+    cudaError_t e = cudaSetDevice(ctx->device);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaSetDevice");
+    cudaStream_t s = stream ? (cudaStream_t)stream : ctx->stream;
+    const int64_t n = batch->n_pairs;
+    if (n == 0) return AGATHA_OK;
+
+    BatchShape shape;
+    if (!dev) {
+        int rc = validate_host_batch(ctx, batch, p, &shape);
+        if (rc) return rc;
+    } else {
+        shape.n = n;
+        shape.max_len = 0;
+        // lengths live on the device: plan for the widest band the parameters allow
+        shape.max_w_all = p.w >= 0 ? p.w : 32 * 32 - 1;
+        shape.max_w_warp = shape.max_w_all;
+        if (batch->q_words < 0 || batch->t_words < 0)
+            return set_error(ctx, AGATHA_EINVAL, "negative stream size");
+    }
+    LaunchPlan lp;
+    int rc = make_plan(ctx, p, shape, flags, &lp);
+    if (rc) return rc;
+    if (dev && p.w < 0 && !lp.plain) {
+        // unbanded device batch: pairs wider than the warp kernel go to the block kernel
+        lp.wide_w = plain_kernel_max_w();
+    }
+    if ((rc = ensure_batch_buffers(ctx, n, batch->q_words, batch->t_words, !dev))) return rc;
+
+    DevBatch *d = ctx->h_desc;
+    // the previous call's descriptor upload must be finished before it is rewritten
+    cudaStreamSynchronize(ctx->last_desc_stream ? ctx->last_desc_stream : s);
+    if (!dev) {
+        const int64_t qw = batch->q_words, tw = batch->t_words;
+        if (qw > 0 && (e = cudaMemcpyAsync(ctx->q_packed.ptr, batch->q_packed, qw * 4,
+                                           cudaMemcpyHostToDevice, s)) != cudaSuccess)
+            return cuda_fail(ctx, e, "copy q_packed");
+        if (tw > 0 && (e = cudaMemcpyAsync(ctx->t_packed.ptr, batch->t_packed, tw * 4,
+                                           cudaMemcpyHostToDevice, s)) != cudaSuccess)
+            return cuda_fail(ctx, e, "copy t_packed");
+        if ((e = cudaMemcpyAsync(ctx->q_off.ptr, batch->q_off, n * 8, cudaMemcpyHostToDevice, s)) ||
+            (e = cudaMemcpyAsync(ctx->t_off.ptr, batch->t_off, n * 8, cudaMemcpyHostToDevice, s)) ||
+            (e = cudaMemcpyAsync(ctx->q_len.ptr, batch->q_len, n * 4, cudaMemcpyHostToDevice, s)) ||
+            (e = cudaMemcpyAsync(ctx->t_len.ptr, batch->t_len, n * 4, cudaMemcpyHostToDevice, s)))
+            return cuda_fail(ctx, e, "copy batch arrays");
+        d->q_packed = (const uint32_t *)ctx->q_packed.ptr;
+        d->t_packed = (const uint32_t *)ctx->t_packed.ptr;
+        d->q_off = (const int64_t *)ctx->q_off.ptr;
+        d->t_off = (const int64_t *)ctx->t_off.ptr;
+        d->q_len = (const int32_t *)ctx->q_len.ptr;
+        d->t_len = (const int32_t *)ctx->t_len.ptr;
+        d->out = (agatha_result *)ctx->out.ptr;
+    } else {
+        d->q_packed = batch->q_packed;
+        d->t_packed = batch->t_packed;
+        d->q_off = batch->q_off;
+        d->t_off = batch->t_off;
+        d->q_len = batch->q_len;
+        d->t_len = batch->t_len;
+        d->out = out;
+    }
+    d->q_words = batch->q_words;
+    d->t_words = batch->t_words;
+    d->n_pairs = n;
+    fill_desc(ctx, d, p, lp);
+    if ((e = cudaMemcpyAsync(ctx->d_desc, d, sizeof(DevBatch), cudaMemcpyHostToDevice, s)) != cudaSuccess)
+        return cuda_fail(ctx, e, "copy descriptor");
+    ctx->last_desc_stream = s;
+    if ((e = run_plan(ctx, lp, s)) != cudaSuccess) return cuda_fail(ctx, e, "launch");
+    if ((e = cudaMemcpyAsync(ctx->h_counters, ctx->counters.ptr, CTR_COUNT * sizeof(int32_t),
+                             cudaMemcpyDeviceToHost, s)) != cudaSuccess)
+        return cuda_fail(ctx, e, "copy counters");
+    if (!dev) {
+        if ((e = cudaMemcpyAsync(out, ctx->out.ptr, n * sizeof(agatha_result), cudaMemcpyDeviceToHost,
+                                 s)) != cudaSuccess)
+            return cuda_fail(ctx, e, "copy results");
+    }
+    if (flags & AGATHA_ASYNC) return AGATHA_OK;
+    if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return cuda_fail(ctx, e, "synchronize");
+    if (ctx->h_counters[CTR_ERR] != DEV_ERR_NONE)
+        return set_error(ctx, AGATHA_EINVAL, "a pair has a bad length, offset or score range");
+    return AGATHA_OK;
+}
+
+extern "C" int64_t agatha_band_cells(int32_t tlen, int32_t qlen, int32_t w) {
+    if (tlen <= 0 || qlen <= 0) return 0;
+    const int32_t we = effective_w(w, tlen, qlen);
+    int64_t total = 0;
+    for (int32_t t = 0; t < tlen; ++t) {
+        const int32_t lo = std::max(0, t - we), hi = std::min(qlen - 1, t + we);
+        if (hi >= lo) total += hi - lo + 1;
+    }
+    return total;
+}
+
+// ------------------------------------------------------------------ packing
+
+static int pack_range(const uint8_t *codes, int64_t lo_word, int64_t hi_word, int64_t n, uint32_t *out,
+                      bool ascii) {
+    static const int8_t lut_init[256] = {0};
+    (void)lut_init;
+    int8_t lut[256];
+    for (int i = 0; i < 256; ++i) lut[i] = -1;
+    if (ascii) {
+        lut['A'] = lut['a'] = 0; lut['C'] = lut['c'] = 1; lut['G'] = lut['g'] = 2; lut['T'] = lut['t'] = 3;
+    } else {
+        lut[0] = 0; lut[1] = 1; lut[2] = 2; lut[3] = 3;
+    }
+    int bad = 0;
+    for (int64_t wi = lo_word; wi < hi_word; ++wi) {
+        uint32_t word = 0;
+        const int64_t base = wi * 16;
+        const int64_t cnt = std::min<int64_t>(16, n - base);
+        for (int64_t k = 0; k < cnt; ++k) {
+            const int8_t c = lut[codes[base + k]];
+            bad |= (c < 0);
+            word |= (uint32_t)(c & 3) << (2 * k);
+        }
+        out[wi] = word;
+    }
+    return bad ? AGATHA_EINVAL : AGATHA_OK;
+}
+
+static int pack_impl(const uint8_t *codes, int64_t n, uint32_t *out, bool ascii) {
+    if (n < 0 || (n > 0 && (!codes || !out))) return AGATHA_EINVAL;
+    const int64_t words = (n + 15) / 16;
+    const int64_t per = 1 << 20;
+    if (words <= per) return pack_range(codes, 0, words, n, out, ascii);
+    unsigned nt = std::max(1u, std::min(16u, std::thread::hardware_concurrency()));
+    std::vector<std::thread> th;
+    std::atomic<int> rc{AGATHA_OK};
+    const int64_t chunk = (words + nt - 1) / nt;
+    for (unsigned i = 0; i < nt; ++i) {
+        const int64_t lo = i * chunk, hi = std::min(words, lo + chunk);
+        if (lo >= hi) break;
+        th.emplace_back([=, &rc] {
+            if (pack_range(codes, lo, hi, n, out, ascii)) rc = AGATHA_EINVAL;
+        });
+    }
+    for (auto &t : th) t.join();
+    return rc.load();
+}
+
+extern "C" int agatha_pack_codes(const uint8_t *codes, int64_t n, uint32_t *out) {
+    return pack_impl(codes, n, out, false);
+}
+
+extern "C" int agatha_pack_ascii(const char *ascii, int64_t n, uint32_t *out) {
+    return pack_impl((const uint8_t *)ascii, n, out, true);
+}

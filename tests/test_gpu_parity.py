@@ -1,0 +1,180 @@
+"""GPU parity: every kernel path must reproduce the CPU oracle bit for bit.
+
+Integer outputs (scores, coordinates, cell counts, flags) are compared for
+exact equality: the method computes exact integers, so the tolerance is 0.
+"""
+import numpy as np
+import pytest
+
+from oracle import oracle as O
+from paper_2403_06478_gb300 import agatha as A
+from paper_2403_06478_gb300 import build as B
+from paper_2403_06478_gb300 import workload as W
+
+pytestmark = pytest.mark.gpu
+
+FIELDS = O.COMPARE_FIELDS
+
+PATHS = {
+    "batched": 0,
+    "plain": A.AGATHA_PLAIN,
+    "edge_only": A.AGATHA_EDGE_PATH_ONLY,
+    "no_sort": A.AGATHA_NO_SORT,
+    "no_graph": A.AGATHA_NO_GRAPH,
+}
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    B.build()
+    c = A.Context(0)
+    yield c
+    c.close()
+
+
+def _assert_same(got, ref, batch, label):
+    bad = A.results_equal(got, ref, FIELDS)
+    if bad.size:
+        i = int(bad[0])
+        diff = {f: (int(got[i][f]), int(ref[i][f])) for f in FIELDS if got[i][f] != ref[i][f]}
+        raise AssertionError(f"{label}: {bad.size} of {got.shape[0]} pairs differ; first pair {i} "
+                             f"(tlen={int(batch.t_len[i])}, qlen={int(batch.q_len[i])}) "
+                             f"got/expected: {diff}")
+
+
+@pytest.mark.parametrize("path", sorted(PATHS))
+def test_small_config_all_paths(ctx, path):
+    batch = W.make_config("small")
+    ref = O.align_batch(batch)
+    got = A.agatha_align_batch(ctx, batch, flags=PATHS[path])
+    _assert_same(got, ref, batch, f"small/{path}")
+    assert int(ref["cells"].sum()) > 0
+
+
+ADVERSARIAL_SCORINGS = [
+    W.Scoring(2, 4, 4, 2, 24, 1, 100, 400, 0),
+    W.Scoring(2, 4, 4, 2, 24, 1, 7, 30, 0),        # narrow band, frequent Z-drop
+    W.Scoring(1, 4, 6, 2, 26, 1, 33, 20, 5),       # HiFi scoring, end bonus
+    W.Scoring(2, 4, 4, 2, 24, 1, -1, -1, 0),       # unbanded, no Z-drop
+    W.Scoring(2, 3, 2, 3, 5, 1, 16, 0, 0),         # zdrop 0: stops at the first drop
+    W.Scoring(3, 2, 0, 1, 2, 0, 31, 10, 0),        # free gap extension on piece 2
+    W.Scoring(2, 4, 4, 2, 4, 2, 127, 200, 0),      # single piece, w = 32*4-1
+    W.Scoring(2, 4, 4, 2, 24, 1, 128, 200, 0),     # w = 32*4: next slot class
+    W.Scoring(2, 4, 4, 2, 24, 1, 511, 400, 0),     # C = 16 exactly full
+    W.Scoring(2, 4, 4, 2, 24, 1, 750, 400, 0),     # C = 24
+    W.Scoring(2, 4, 4, 2, 24, 1, 1000, 400, 0),    # C = 32
+]
+
+
+def _adversarial_batch(rng, scoring):
+    qs, ts = [], []
+    w = scoring.w if scoring.w > 0 else 64
+    lens = [0, 1, 2, 3, 5, 16, 17, 31, 32, 33, 63, 64, 65, 100, 200, 333, 600, 1200]
+    for L in lens:
+        q = rng.integers(0, 4, L).astype(np.uint8)
+        qs.append(q); ts.append(q.copy())                                   # identical
+        qs.append(q); ts.append(((q + 1) % 4).astype(np.uint8))             # all mismatch
+        qs.append(np.zeros(L, np.uint8)); ts.append(np.zeros(L + 3, np.uint8))   # homopolymer
+        t = rng.integers(0, 4, max(0, L + int(rng.integers(-w - 2, w + 3)))).astype(np.uint8)
+        qs.append(q); ts.append(t)                                          # length gap near w
+        mq = q.copy()
+        if L:
+            mq[rng.integers(0, L, max(1, L // 20))] = rng.integers(0, 4, max(1, L // 20))
+        qs.append(mq); ts.append(np.concatenate([q[: L // 2], rng.integers(0, 4, L - L // 2)]).astype(np.uint8))
+    b2 = W.random_pairs(rng, 60, 400, scoring, min_len=0, related=0.7)
+    for i in range(b2.n_pairs):
+        qs.append(b2.query(i)); ts.append(b2.target(i))
+    return W.from_pairs(qs, ts, scoring, name="adversarial")
+
+
+@pytest.mark.parametrize("si", range(len(ADVERSARIAL_SCORINGS)))
+def test_adversarial_pairs(ctx, si):
+    scoring = ADVERSARIAL_SCORINGS[si]
+    batch = _adversarial_batch(np.random.default_rng(100 + si), scoring)
+    ref = O.align_batch(batch)
+    for path in ("batched", "plain", "edge_only"):
+        got = A.agatha_align_batch(ctx, batch, flags=PATHS[path])
+        _assert_same(got, ref, batch, f"adversarial[{si}]/{path}")
+
+
+def test_empty_batch_and_empty_pairs(ctx):
+    b = W.from_pairs([], [], W.SMALL_SCORING)
+    assert A.agatha_align_batch(ctx, b).shape[0] == 0
+    b = W.from_pairs(["", "A", ""], ["", "", "ACGT"], W.SMALL_SCORING)
+    got = A.agatha_align_batch(ctx, b)
+    for r in got:
+        assert (r["max"], r["qe"], r["te"], r["gscore"], r["cells"], r["zdropped"]) == (
+            0, -1, -1, A.NEG_INF, 0, 0)
+
+
+def test_results_independent_of_batch_composition(ctx):
+    full = W.make_config("ont", n_pairs=400)
+    ref = A.agatha_align_batch(ctx, full)
+    idx = np.random.default_rng(5).permutation(400)[:150]
+    sub = A.agatha_align_batch(ctx, full.subset(idx))
+    bad = A.results_equal(sub, ref[idx])
+    assert bad.size == 0
+
+
+def _sampled_parity(ctx, name, n_sample, seed):
+    batch = W.make_config(name)                    # full size, bench launch configuration
+    got = A.agatha_align_batch(ctx, batch)
+    rng = np.random.default_rng(seed)
+    # the longest pairs and a uniform sample: the oracle computes them one by one
+    longest = np.argsort(-(batch.q_len.astype(np.int64) + batch.t_len))[:8]
+    idx = np.unique(np.concatenate([longest, rng.choice(batch.n_pairs, n_sample, replace=False)]))
+    ref = O.align_batch(batch, idx=idx)
+    _assert_same(got[idx], ref, batch.subset(idx), f"{name}/sampled")
+    # properties that hold for every pair
+    assert (got["cells"] > 0).all() == (batch.q_len > 0).all()
+    assert set(np.unique(got["zdropped"])) <= {0, 1}
+    assert (got["max"] >= 0).all()
+    return batch, got
+
+
+def test_ont_full_size_sampled(ctx):
+    batch, got = _sampled_parity(ctx, "ont", 250, 1)
+    # the plain kernel agrees with the batched one on every pair
+    plain = A.agatha_align_batch(ctx, batch, flags=A.AGATHA_PLAIN)
+    assert A.results_equal(plain, got).size == 0
+
+
+def test_hifi_full_size_sampled(ctx):
+    _sampled_parity(ctx, "hifi", 120, 2)
+
+
+def test_skewed_full_size_sampled(ctx):
+    _sampled_parity(ctx, "skewed", 400, 3)
+
+
+def test_host_batch_errors_before_launch(ctx):
+    batch = W.make_config("small", n_pairs=4)
+    pb = A.pack_batch(batch)
+    pb.q_off = pb.q_off.copy()
+    pb.q_off[2] = int(pb.q_packed.shape[0]) * 16      # outside the stream
+    with pytest.raises(A.AgathaError) as e:
+        ctx.align_host(pb, batch.scoring)
+    assert e.value.code == A.AGATHA_EINVAL
+    with pytest.raises(A.AgathaError) as e:
+        ctx.align_host(A.pack_batch(batch), W.Scoring(w=0))
+    assert e.value.code == A.AGATHA_EINVAL
+
+
+def test_device_pointers_and_device_side_check(ctx):
+    torch = pytest.importorskip("torch")
+    batch = W.make_config("small", n_pairs=64)
+    pb = A.pack_batch(batch)
+    dev = {k: torch.from_numpy(getattr(pb, k)).cuda() for k in
+           ("q_packed", "t_packed", "q_off", "t_off", "q_len", "t_len")}
+    out = torch.zeros(pb.n_pairs * 48, dtype=torch.uint8, device="cuda")
+    for flags in (0, A.AGATHA_PLAIN):
+        ctx.align_device(dev["q_packed"], dev["t_packed"], dev["q_off"], dev["t_off"], dev["q_len"],
+                         dev["t_len"], out, batch.scoring, flags=flags)
+        got = out.cpu().numpy().view(A.RESULT_DTYPE)
+        _assert_same(got, O.align_batch(batch), batch, f"device/{flags}")
+    bad_off = dev["t_off"].clone()
+    bad_off[5] = int(pb.t_packed.shape[0]) * 16 + 100
+    with pytest.raises(A.AgathaError) as e:
+        ctx.align_device(dev["q_packed"], dev["t_packed"], dev["q_off"], bad_off, dev["q_len"],
+                         dev["t_len"], out, batch.scoring)
+    assert e.value.code == A.AGATHA_EINVAL
