@@ -1,0 +1,344 @@
+#!/usr/bin/env python
+"""Benchmark of banded two-piece-affine Z-drop extension alignment on GB300.
+
+One step = one pass of the whole hot path (validation, longest-first ordering,
+the batched warp kernel) over one batch of synthetic ONT-like pairs (20,000
+pairs, log-normal lengths with median 5 kbp, 12% errors, 10% divergent tails,
+w=500, zdrop=400).  Printed as one JSON line:
+
+  value       GCUPS of the batched kernel path, inputs resident in HBM, CUDA
+              events on the launching stream, L2 flushed between steps
+  e2e         the same metric through agatha_align_batch with pinned HOST
+              buffers (host->device copies and result read-back included)
+  plain       the plain one-pair-per-block kernel on the same batch
+  roofline    the warp kernel against the integer issue rate of the GPU
+  cpu_baseline the CPU oracle on a bounded sample of the same workload
+
+``--impl reference`` times the CPU oracle as the reference arm instead.
+Multi-GPU (torchrun): every rank aligns its own batch (weak scaling, no
+collective on the data path); rank 0 prints the aggregate.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+METRIC = "GCUPS & pairs/s on ONT-like mix: batched vs plain GPU kernel, bit-exact"
+WORKLOAD = ("ont: 20000 pairs, query log-normal (median 5 kbp, sigma 0.8, clip 500-50k), "
+            "target 5% sub / 4% del / 3% ins, 10% divergent tails, a=2 b=4 q=4 e=2 q2=24 e2=1, "
+            "w=500, zdrop=400")
+L2_FLUSH_BYTES = 512 << 20          # > 129 MB of L2
+OPS_PER_CELL_I32 = 13               # issued int32 lane-ops per cell, see the design doc
+CPU_SAMPLE_PAIRS = 6000
+REF_STEP_PAIRS = 300
+
+
+def _env_int(name, default):
+    try:
+        return int(os.environ.get(name, default))
+    except ValueError:
+        return default
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms."""
+
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(prefix="clocks", suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.QUERY}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        os.unlink(self.path)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "samples": len(sm),
+                "reasons": sorted(reasons)}
+
+
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as fh:
+            return json.load(fh), "measured"
+    return {"hbm_gbs": 6800.0, "sm_max_mhz": 2070.0}, "fallback"
+
+
+def traffic_from_profile():
+    """DRAM bytes per launch of the warp kernel from the committed ncu summary."""
+    path = os.path.join(ROOT, "profiles", "warp_kernel_ont_traffic.json")
+    if not os.path.exists(path):
+        return None
+    with open(path) as fh:
+        d = json.load(fh)
+    return d.get("dram_bytes_per_launch")
+
+
+def cpu_baseline(batch, n_sample: int, seed: int = 7):
+    from oracle import oracle as O      # the CPU oracle: timed here as a reported baseline
+    rng = np.random.default_rng(seed)
+    idx = np.sort(rng.choice(batch.n_pairs, min(n_sample, batch.n_pairs), replace=False))
+    cores = os.cpu_count() or 1
+    O.align_batch(batch, idx=idx[:8], threads=cores)     # load + warm
+    t0 = time.perf_counter()
+    res = O.align_batch(batch, idx=idx, threads=cores)
+    dt = time.perf_counter() - t0
+    cells = int(res["cells"].sum())
+    return {"value": round(cells / dt / 1e9, 4), "unit": "GCUPS", "cores": cores, "kind": "oracle",
+            "sample": f"{idx.size} seeded random pairs of the workload ({cells} cells, {dt:.1f} s)"}
+
+
+def run_reference(args):
+    """Reference arm: the CPU oracle on bounded samples of the same workload."""
+    rank = _env_int("RANK", 0)
+    if rank != 0:
+        return 0
+    from paper_2403_06478_gb300 import workload as W
+    from oracle import oracle as O
+    batch = W.make_config("ont")
+    cores = os.cpu_count() or 1
+    rng = np.random.default_rng(11)
+    perm = rng.permutation(batch.n_pairs)
+
+    def sample(k):
+        lo = (k * REF_STEP_PAIRS) % batch.n_pairs
+        return np.sort(perm[lo:lo + REF_STEP_PAIRS])
+
+    O.build()
+    for k in range(args.warmup):
+        O.align_batch(batch, idx=sample(k), threads=cores)
+    total_cells, total_s, total_pairs = 0, 0.0, 0
+    for k in range(args.steps):
+        idx = sample(args.warmup + k)
+        t0 = time.perf_counter()
+        res = O.align_batch(batch, idx=idx, threads=cores)
+        total_s += time.perf_counter() - t0
+        total_cells += int(res["cells"].sum())
+        total_pairs += idx.size
+    gcups = total_cells / total_s / 1e9
+    line = {
+        "impl": "reference", "metric": METRIC, "value": round(gcups, 4), "unit": "GCUPS",
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": round(total_s / max(args.steps, 1) * 1e3, 3), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "int64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "step": f"{REF_STEP_PAIRS} pairs per step (bounded sample)"},
+        "pairs_per_s": round(total_pairs / total_s, 2),
+        "cpu_baseline": {"value": round(gcups, 4), "unit": "GCUPS", "cores": cores, "kind": "oracle",
+                         "sample": f"{args.steps} steps x {REF_STEP_PAIRS} seeded random pairs"},
+        "e2e": {"value": round(gcups, 4), "unit": "GCUPS", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--plain-steps", type=int, default=3)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-sample-pairs", type=int, default=CPU_SAMPLE_PAIRS)
+    args = ap.parse_args()
+    args.warmup = max(args.warmup, 3)
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import torch
+    from paper_2403_06478_gb300 import agatha as A
+    from paper_2403_06478_gb300 import build as B
+    from paper_2403_06478_gb300 import workload as W
+
+    rank, world, local = _env_int("RANK", 0), _env_int("WORLD_SIZE", 1), _env_int("LOCAL_RANK", 0)
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    B.build()
+
+    # each rank aligns its own batch: rank 0 the standard workload, others reseeded
+    batch = W.make_config("ont", seed=None if rank == 0 else W.SEED_BASE + 2 + 1000 * rank)
+    pb = A.pack_batch(batch)
+    n = pb.n_pairs
+    ctx = A.Context(local, timing=True)
+    # a dedicated stream: every launch, copy and timing event of the step sits on it
+    stream = torch.cuda.Stream()
+    torch.cuda.set_stream(stream)
+    sh = stream.cuda_stream
+    dev = {k: torch.from_numpy(getattr(pb, k)).to("cuda", non_blocking=False)
+           for k in ("q_packed", "t_packed", "q_off", "t_off", "q_len", "t_len")}
+    out = torch.empty(n * 48, dtype=torch.uint8, device="cuda")
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device="cuda")
+
+    def run_dev(flags):
+        ctx.align_device(dev["q_packed"], dev["t_packed"], dev["q_off"], dev["t_off"], dev["q_len"],
+                         dev["t_len"], out, batch.scoring, flags=flags | A.AGATHA_ASYNC, stream=sh)
+
+    def timed(flags, steps, warmup, sampler=None):
+        for _ in range(warmup):
+            run_dev(flags)
+        torch.cuda.synchronize()
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+        if sampler:
+            sampler.start()
+        step_ms, kern_ms = [], []
+        for k in range(steps):
+            flush.fill_(k & 0xff)                      # evict L2 between steps (not timed)
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            run_dev(flags)
+            e1.record(stream)
+            e1.synchronize()
+            step_ms.append(e0.elapsed_time(e1))
+            kern_ms.append(ctx.last_kernel_ms())
+        torch.cuda.synchronize()
+        clocks = sampler.stop() if sampler else None
+        res = out.cpu().numpy().view(A.RESULT_DTYPE).copy()
+        return step_ms, kern_ms, res, clocks
+
+    sampler = ClockSampler(local)
+    step_ms, kern_ms, res, clocks = timed(0, args.steps, args.warmup, sampler)
+    cells = int(res["cells"].sum())
+    plain_ms, plain_kern, plain_res, _ = timed(A.AGATHA_PLAIN, max(1, args.plain_steps), 1)
+    bit_exact = bool(A.results_equal(res, plain_res).size == 0)
+
+    # end to end: pinned host buffers through the C ABI, copies inside the timed region
+    pin = {k: torch.from_numpy(getattr(pb, k)).pin_memory() for k in
+           ("q_packed", "t_packed", "q_off", "t_off", "q_len", "t_len")}
+    pin_pb = A.PackedBatch(*[pin[k].numpy() for k in
+                             ("q_packed", "t_packed", "q_off", "t_off", "q_len", "t_len")])
+    host_out = torch.empty(n * 48, dtype=torch.uint8).pin_memory().numpy().view(A.RESULT_DTYPE)
+    for _ in range(args.warmup):
+        ctx.align_host(pin_pb, batch.scoring, stream=sh, out=host_out)
+    torch.cuda.synchronize()
+    e2e_ms = []
+    for k in range(args.steps):
+        flush.fill_(k & 0xff)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        ctx.align_host(pin_pb, batch.scoring, stream=sh, out=host_out)
+        e1.record(stream)
+        e1.synchronize()
+        e2e_ms.append(e0.elapsed_time(e1))
+    e2e_exact = bool(A.results_equal(host_out, res).size == 0)
+    h2d = pin_pb.nbytes()
+    d2h = n * 48 + 32
+
+    # aggregate over ranks: units all ranks processed / the slowest rank's time
+    tot_ms, e2e_tot = sum(step_ms), sum(e2e_ms)
+    agg = torch.tensor([float(cells), tot_ms, e2e_tot, float(n)], dtype=torch.float64, device="cuda")
+    if dist is not None:
+        cells_t = agg[[0, 3]].clone()
+        dist.all_reduce(cells_t, op=dist.ReduceOp.SUM)
+        times_t = agg[[1, 2]].clone()
+        dist.all_reduce(times_t, op=dist.ReduceOp.MAX)
+        all_cells, all_pairs = float(cells_t[0]), float(cells_t[1])
+        tot_ms, e2e_tot = float(times_t[0]), float(times_t[1])
+    else:
+        all_cells, all_pairs = float(cells), float(n)
+    value = all_cells * args.steps / (tot_ms / 1e3) / 1e9
+    e2e_value = all_cells * args.steps / (e2e_tot / 1e3) / 1e9
+
+    if rank != 0:
+        if dist is not None:
+            dist.destroy_process_group()
+        return 0
+
+    peaks, peak_kind = measured_peaks()
+    props = torch.cuda.get_device_properties(local)
+    n_sm = props.multi_processor_count
+    sm_max_mhz = float(peaks.get("sm_max_mhz", 2070.0))
+    int_peak = n_sm * 128 * sm_max_mhz * 1e6 / 1e12         # Tops/s of int32 lanes
+    k_ms = statistics.mean(kern_ms)
+    achieved = cells * OPS_PER_CELL_I32 / (k_ms / 1e3) / 1e12
+    line = {
+        "metric": METRIC, "value": round(value, 3), "unit": "GCUPS", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": round(tot_ms / args.steps, 3), "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "int32", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "pairs_per_gpu": n, "cells_per_step": cells,
+                   "l2": "flushed between steps (512 MB write)", "inputs": "resident in HBM"},
+        "pairs_per_s": round(all_pairs * args.steps / (tot_ms / 1e3), 1),
+        "plain": {"value": round(all_cells / (statistics.mean(plain_ms) / 1e3) / 1e9, 3)
+                  if world == 1 else round(cells / (statistics.mean(plain_ms) / 1e3) / 1e9, 3),
+                  "unit": "GCUPS", "ms_per_step": round(statistics.mean(plain_ms), 3),
+                  "kernel_ms": round(statistics.mean(plain_kern), 3),
+                  "pairs_per_s": round(n / (statistics.mean(plain_ms) / 1e3), 1)},
+        "batched_vs_plain": round(statistics.mean(plain_ms) / (tot_ms / args.steps), 3),
+        "bit_exact_batched_vs_plain": bit_exact,
+        "e2e": {"value": round(e2e_value, 3), "unit": "GCUPS", "h2d_bytes_per_step": int(h2d),
+                "d2h_bytes_per_step": int(d2h), "bit_exact": e2e_exact,
+                "ms_per_step": round(e2e_tot / args.steps, 3)},
+        "gpu_launches": 4 * args.steps,
+        "roofline": {"bound": "alu", "achieved": round(achieved, 3),
+                     "peak": round(int_peak, 3), "unit": "Tops/s", "frac": round(achieved / int_peak, 4),
+                     "traffic": traffic_from_profile(), "kernel": "warp_align_kernel",
+                     "kernel_ms": round(k_ms, 3), "ops_per_cell": OPS_PER_CELL_I32,
+                     "peak_basis": f"{n_sm} SMs x 128 int32 lanes x {sm_max_mhz:.0f} MHz ({peak_kind})"},
+        "clocks": clocks,
+    }
+    if world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(batch, args.cpu_sample_pairs)
+    print(json.dumps(line), flush=True)
+    ctx.close()
+    if dist is not None:
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -66,6 +66,10 @@ extern "C" {
 #define AGATHA_EDGE_PATH_ONLY 0x40u /* batched kernel: run every anti-diagonal
                                      through the masked edge path (testing)  */
 
+/* Flags for agatha_config.flags. */
+#define AGATHA_CFG_TIMING  0x1    /* record CUDA events around the main kernel
+                                     of every batch (agatha_last_kernel_ms)   */
+
 typedef struct agatha_ctx agatha_ctx;
 
 /* Scoring and guiding parameters (minimap2 naming).
@@ -150,6 +154,13 @@ void agatha_destroy(agatha_ctx *ctx);
 int agatha_align_batch(agatha_ctx *ctx, const agatha_batch *batch,
                        const agatha_params *params, agatha_result *out,
                        uint32_t flags, void *stream);
+
+/* Duration in milliseconds of the main alignment kernel of the last batch
+ * run on ctx (the warp kernel of the batched path, the block kernel of the
+ * plain path), from CUDA events recorded around its launch on its stream.
+ * Waits for the end event.  ENOTSUP unless the context was created with
+ * AGATHA_CFG_TIMING; EAGAIN before the first batch. */
+int agatha_last_kernel_ms(agatha_ctx *ctx, float *ms);
 
 /* Check parameters on the host without touching the GPU: AGATHA_OK or
  * AGATHA_EINVAL.  `normalised` (may be NULL) receives the parameters the

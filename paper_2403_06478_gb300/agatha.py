@@ -37,6 +37,8 @@ AGATHA_FORCE32 = 0x10
 AGATHA_NO_GRAPH = 0x20
 AGATHA_EDGE_PATH_ONLY = 0x40
 
+AGATHA_CFG_TIMING = 0x1
+
 NEG_INF = -0x40000000
 
 RESULT_DTYPE = np.dtype([
@@ -103,6 +105,7 @@ _SIGS = {
     "agatha_pack_codes": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p]),
     "agatha_pack_ascii": (ctypes.c_int, [ctypes.c_char_p, ctypes.c_int64, ctypes.c_void_p]),
     "agatha_band_cells": (ctypes.c_int64, [ctypes.c_int32, ctypes.c_int32, ctypes.c_int32]),
+    "agatha_last_kernel_ms": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_float)]),
     "agatha_serve_start": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(agatha_serve_config)]),
     "agatha_serve_submit": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(agatha_batch),
                                            ctypes.POINTER(agatha_params), ctypes.c_void_p,
@@ -218,9 +221,9 @@ class Context:
     """An ``agatha_ctx`` on one device."""
 
     def __init__(self, device: int = 0, mem_budget_bytes: int = 0, max_pairs: int = 0,
-                 tune_cache_path: Optional[str] = None):
+                 tune_cache_path: Optional[str] = None, timing: bool = False):
         self._ptr = ctypes.c_void_p()
-        cfg = agatha_config(device, 0, mem_budget_bytes, max_pairs,
+        cfg = agatha_config(device, AGATHA_CFG_TIMING if timing else 0, mem_budget_bytes, max_pairs,
                             tune_cache_path.encode() if tune_cache_path else None)
         _check(lib().agatha_init(ctypes.byref(self._ptr), ctypes.byref(cfg)), what="agatha_init")
 
@@ -244,6 +247,12 @@ class Context:
 
     def __exit__(self, *exc):
         self.close()
+
+    def last_kernel_ms(self) -> float:
+        ms = ctypes.c_float()
+        _check(lib().agatha_last_kernel_ms(self._ptr, ctypes.byref(ms)), self._ptr,
+               "agatha_last_kernel_ms")
+        return float(ms.value)
 
     def last_error(self) -> str:
         return lib().agatha_last_error(self._ptr).decode()

@@ -176,40 +176,37 @@ int warp_occupancy(int C) {
 }
 
 // Enqueue the device work of one batch whose descriptor is already on the
-// device.  Captured into a CUDA graph unless the caller asked otherwise.
-static cudaError_t enqueue_batch(agatha_ctx *ctx, const LaunchPlan &lp, cudaStream_t s) {
-    cudaError_t e = cudaMemsetAsync(ctx->counters.ptr, 0, CTR_COUNT * sizeof(int32_t), s);
-    if (e != cudaSuccess) return e;
-    if (lp.plain) {
-        // validation only (no sort), then the plain kernel over every pair
-        e = launch_prep(ctx->d_desc, lp.n, 0, s, ctx->n_sm);
+// device, in two parts: part 0 = validation and ordering, part 1 = the
+// alignment kernels.  Each part is captured into its own CUDA graph (unless
+// the caller asked otherwise) so the timing events can sit between them.
+static cudaError_t enqueue_part(agatha_ctx *ctx, const LaunchPlan &lp, int part, cudaStream_t s) {
+    cudaError_t e = cudaSuccess;
+    if (part == 0) {
+        e = cudaMemsetAsync(ctx->counters.ptr, 0, CTR_COUNT * sizeof(int32_t), s);
         if (e != cudaSuccess) return e;
-        return launch_plain_kernel(ctx->d_desc, lp.plain_blocks, lp.plain_w, 0, s);
+        if (!lp.plain) {
+            e = cudaMemsetAsync(ctx->hist.ptr, 0, 256 * sizeof(int64_t), s);
+            if (e != cudaSuccess) return e;
+        }
+        // the plain path only validates (no sort); the batched path also orders
+        return launch_prep(ctx->d_desc, lp.n, lp.plain ? 0 : lp.sort, s, ctx->n_sm);
     }
-    e = cudaMemsetAsync(ctx->hist.ptr, 0, 256 * sizeof(int64_t), s);
-    if (e != cudaSuccess) return e;
-    e = launch_prep(ctx->d_desc, lp.n, lp.sort, s, ctx->n_sm);
-    if (e != cudaSuccess) return e;
+    if (lp.plain) return launch_plain_kernel(ctx->d_desc, lp.plain_blocks, lp.plain_w, 0, s);
     e = launch_warp(lp.C, ctx->d_desc, lp.warp_blocks, s, lp.fast);
     if (e != cudaSuccess) return e;
     if (lp.wide_w > 0) e = launch_plain_kernel(ctx->d_desc, (int64_t)ctx->n_sm * 2, lp.wide_w, 1, s);
     return e;
 }
 
-static cudaError_t run_plan(agatha_ctx *ctx, const LaunchPlan &lp, cudaStream_t s) {
-    if (!lp.use_graph) return enqueue_batch(ctx, lp, s);
-    if (ctx->graphs_stale) {
-        for (auto &kv : ctx->graphs) cudaGraphExecDestroy(kv.second);
-        ctx->graphs.clear();
-        ctx->graphs_stale = false;
-    }
-    const auto key = lp.key();
+static cudaError_t launch_part(agatha_ctx *ctx, const LaunchPlan &lp, int part, cudaStream_t s) {
+    if (!lp.use_graph) return enqueue_part(ctx, lp, part, s);
+    const auto key = std::make_tuple(part, lp.key());
     auto it = ctx->graphs.find(key);
     if (it == ctx->graphs.end()) {
         cudaGraph_t g = nullptr;
         cudaError_t e = cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal);
         if (e != cudaSuccess) return e;
-        cudaError_t e1 = enqueue_batch(ctx, lp, s);
+        cudaError_t e1 = enqueue_part(ctx, lp, part, s);
         e = cudaStreamEndCapture(s, &g);
         if (e1 != cudaSuccess) { if (g) cudaGraphDestroy(g); return e1; }
         if (e != cudaSuccess) return e;
@@ -220,6 +217,20 @@ static cudaError_t run_plan(agatha_ctx *ctx, const LaunchPlan &lp, cudaStream_t 
         it = ctx->graphs.emplace(key, ge).first;
     }
     return cudaGraphLaunch(it->second, s);
+}
+
+static cudaError_t run_plan(agatha_ctx *ctx, const LaunchPlan &lp, cudaStream_t s) {
+    if (ctx->graphs_stale) {
+        for (auto &kv : ctx->graphs) cudaGraphExecDestroy(kv.second);
+        ctx->graphs.clear();
+        ctx->graphs_stale = false;
+    }
+    cudaError_t e = launch_part(ctx, lp, 0, s);
+    if (e != cudaSuccess) return e;
+    if (ctx->timing && (e = cudaEventRecord(ctx->ev_k0, s)) != cudaSuccess) return e;
+    if ((e = launch_part(ctx, lp, 1, s)) != cudaSuccess) return e;
+    if (ctx->timing) e = cudaEventRecord(ctx->ev_k1, s);
+    return e;
 }
 
 int ensure_batch_buffers(agatha_ctx *ctx, int64_t n, int64_t q_words, int64_t t_words,
@@ -339,6 +350,13 @@ extern "C" int agatha_init(agatha_ctx **out, const agatha_config *cfg) {
         agatha_destroy(ctx);
         return AGATHA_ENOMEM;
     }
+    if (c.flags & AGATHA_CFG_TIMING) {
+        ctx->timing = true;
+        if (cudaEventCreate(&ctx->ev_k0) != cudaSuccess || cudaEventCreate(&ctx->ev_k1) != cudaSuccess) {
+            agatha_destroy(ctx);
+            return AGATHA_ECUDA;
+        }
+    }
     if ((e = plain_kernel_prepare()) != cudaSuccess) {
         agatha_destroy(ctx);
         return AGATHA_ECUDA;
@@ -359,6 +377,8 @@ extern "C" void agatha_destroy(agatha_ctx *ctx) {
                       &ctx->t_len, &ctx->out, &ctx->order, &ctx->wide_order, &ctx->counters,
                       &ctx->hist, &ctx->desc};
     for (DevBuf *b : bufs) b->release();
+    if (ctx->ev_k0) cudaEventDestroy(ctx->ev_k0);
+    if (ctx->ev_k1) cudaEventDestroy(ctx->ev_k1);
     if (ctx->h_desc) cudaFreeHost(ctx->h_desc);
     if (ctx->h_counters) cudaFreeHost(ctx->h_counters);
     if (ctx->stream) cudaStreamDestroy(ctx->stream);
@@ -451,6 +471,7 @@ extern "C" int agatha_align_batch(agatha_ctx *ctx, const agatha_batch *batch,
         return cuda_fail(ctx, e, "copy descriptor");
     ctx->last_desc_stream = s;
     if ((e = run_plan(ctx, lp, s)) != cudaSuccess) return cuda_fail(ctx, e, "launch");
+    ctx->timed_once = true;
     if ((e = cudaMemcpyAsync(ctx->h_counters, ctx->counters.ptr, CTR_COUNT * sizeof(int32_t),
                              cudaMemcpyDeviceToHost, s)) != cudaSuccess)
         return cuda_fail(ctx, e, "copy counters");
@@ -464,6 +485,15 @@ extern "C" int agatha_align_batch(agatha_ctx *ctx, const agatha_batch *batch,
     if (ctx->h_counters[CTR_ERR] != DEV_ERR_NONE)
         return set_error(ctx, AGATHA_EINVAL, "a pair has a bad length, offset or score range");
     return AGATHA_OK;
+}
+
+extern "C" int agatha_last_kernel_ms(agatha_ctx *ctx, float *ms) {
+    if (!ctx || !ms) return AGATHA_EINVAL;
+    if (!ctx->timing) return AGATHA_ENOTSUP;
+    if (!ctx->timed_once) return AGATHA_EAGAIN;
+    cudaError_t e = cudaEventSynchronize(ctx->ev_k1);
+    if (e == cudaSuccess) e = cudaEventElapsedTime(ms, ctx->ev_k0, ctx->ev_k1);
+    return e == cudaSuccess ? AGATHA_OK : cuda_fail(ctx, e, "kernel timing");
 }
 
 extern "C" int64_t agatha_band_cells(int32_t tlen, int32_t qlen, int32_t w) {

@@ -78,6 +78,9 @@ struct agatha_ctx {
     agatha::DevBatch *h_desc = nullptr;
     int32_t *h_counters = nullptr;
     bool graphs_stale = false;
-    std::map<std::tuple<int, int, int, int, int32_t, int>, cudaGraphExec_t> graphs;
+    std::map<std::tuple<int, std::tuple<int, int, int, int, int32_t, int>>, cudaGraphExec_t> graphs;
     ServeState *serve = nullptr;
+    bool timing = false;               // AGATHA_CFG_TIMING
+    bool timed_once = false;
+    cudaEvent_t ev_k0 = nullptr, ev_k1 = nullptr;
 };
