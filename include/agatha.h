@@ -225,6 +225,34 @@ int agatha_serve_stats_get(agatha_ctx *ctx, agatha_serve_stats *stats);
 int agatha_serve_stop(agatha_ctx *ctx, int32_t drain);
 
 /* ---------------------------------------------------------------------- */
+/* Allocation-free alignment.  The paper has no counterpart: this entry point
+ * exists for callers that cannot let a library call cudaMalloc or cudaFree -
+ * for example a host application that reserves all device memory up front and
+ * only hands out pointers into it, or one that must not pay the device-wide
+ * synchronisation cudaFree implies in the middle of its work.
+ *
+ * It runs the same batched path as agatha_align_batch (validation, ordering,
+ * warp kernel) on the current device and allocates nothing.  The scratch
+ * memory the path needs (descriptor, queue counters, ordering lists) sits in a
+ * fixed device array of the library, about 0.5 MiB, sized for at most
+ * AGATHA_NOALLOC_MAX_PAIRS pairs; every GPU that loads the library keeps that
+ * array until the process exits.
+ *   batch: every array is device memory of the current device.
+ *   out:   device memory for batch->n_pairs results.
+ *   stream: cudaStream_t (NULL: the legacy default stream).  The call waits
+ *          for its work on that stream before returning.
+ * The first call on a device looks up the array's device address and
+ * prepares the kernels; make that first call before any stream capture.
+ * All calls share the one array and it keeps the last call's contents (the
+ * call clears what must start at zero): calls whose work overlaps on the GPU
+ * (other streams or host threads) race, so the caller must serialise them.
+ * Errors: EINVAL (n_pairs > AGATHA_NOALLOC_MAX_PAIRS, bad parameters, a pair
+ * outside its stream), ENOTSUP (band wider than supported), ECUDA. */
+#define AGATHA_NOALLOC_MAX_PAIRS 65536
+int agatha_align_batch_noalloc(const agatha_batch *batch, const agatha_params *params,
+                               agatha_result *out, void *stream);
+
+/* ---------------------------------------------------------------------- */
 
 const char *agatha_strerror(int code);
 const char *agatha_last_error(agatha_ctx *ctx);

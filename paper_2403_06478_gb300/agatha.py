@@ -106,6 +106,9 @@ _SIGS = {
     "agatha_pack_ascii": (ctypes.c_int, [ctypes.c_char_p, ctypes.c_int64, ctypes.c_void_p]),
     "agatha_band_cells": (ctypes.c_int64, [ctypes.c_int32, ctypes.c_int32, ctypes.c_int32]),
     "agatha_last_kernel_ms": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_float)]),
+    "agatha_align_batch_noalloc": (ctypes.c_int, [ctypes.POINTER(agatha_batch),
+                                                  ctypes.POINTER(agatha_params), ctypes.c_void_p,
+                                                  ctypes.c_void_p]),
     "agatha_serve_start": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(agatha_serve_config)]),
     "agatha_serve_submit": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(agatha_batch),
                                            ctypes.POINTER(agatha_params), ctypes.c_void_p,
@@ -293,6 +296,31 @@ class Context:
                                       ctypes.c_uint32(flags | AGATHA_DEVICE_PTRS),
                                       ctypes.c_void_p(stream) if stream else None)
         _check(rc, self._ptr, "agatha_align_batch")
+
+
+AGATHA_NOALLOC_MAX_PAIRS = 65536
+
+
+def agatha_align_batch_noalloc(q_packed, t_packed, q_off, t_off, q_len, t_len, out, scoring,
+                               stream: int = 0, n_pairs: Optional[int] = None) -> None:
+    """The allocation-free entry point on device tensors (torch CUDA tensors or
+    raw pointers).  ``out`` holds n_pairs * 48 bytes of device memory."""
+    def ptr(x):
+        if x is None:
+            return None
+        return int(x.data_ptr()) if hasattr(x, "data_ptr") else int(x)
+
+    def numel(x):
+        return 0 if x is None else (int(x.numel()) if hasattr(x, "numel") else int(len(x)))
+
+    n = numel(q_len) if n_pairs is None else int(n_pairs)
+    b = agatha_batch(n, ptr(q_packed), ptr(t_packed), numel(q_packed), numel(t_packed),
+                     ptr(q_off), ptr(t_off), ptr(q_len), ptr(t_len))
+    p = make_params(scoring)
+    _check(lib().agatha_align_batch_noalloc(ctypes.byref(b), ctypes.byref(p),
+                                            ctypes.c_void_p(ptr(out)) if out is not None else None,
+                                            ctypes.c_void_p(stream) if stream else None),
+           what="agatha_align_batch_noalloc")
 
 
 def agatha_init(device: int = 0, **kw) -> Context:
