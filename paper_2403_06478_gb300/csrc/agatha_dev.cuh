@@ -50,13 +50,17 @@ struct DevBatch {
                              // [3] error word
     int32_t *wide_order;     // pairs whose band is too wide for the warp kernel
     int64_t *bucket_hist;    // scratch for the ordering
+    int32_t *ovf_list;       // pairs the 16-bit kernel hands back to the 32-bit one
     DevParams params;
     int32_t warp_w_max;      // widest band the warp kernel takes (32*C - 1)
     int32_t pad;
 };
 
 enum : int32_t { CTR_HEAD = 0, CTR_NWARP = 1, CTR_NWIDE = 2, CTR_ERR = 3, CTR_WIDE_HEAD = 4,
-                 CTR_COUNT = 8 };
+                 CTR_NOVF = 5, CTR_OVF_HEAD = 6, CTR_COUNT = 8 };
+
+// Which pair list a warp kernel launch walks.
+enum : int32_t { WARP_LIST_MAIN = 0, WARP_LIST_OVERFLOW = 1 };
 
 // device error codes written to counters[CTR_ERR]
 enum : int32_t { DEV_ERR_NONE = 0, DEV_ERR_BAD_PAIR = 1 };
@@ -144,9 +148,14 @@ __device__ __forceinline__ bool pair_valid(const DevBatch &B, int64_t i) {
 cudaError_t launch_prep(const DevBatch *d_batch, int64_t n_pairs, int32_t sort, cudaStream_t s,
                         int n_sm);
 template <int C>
-cudaError_t launch_warp_c(const DevBatch *d_batch, int n_blocks, cudaStream_t s, int use_fast);
+cudaError_t launch_warp_c(const DevBatch *d_batch, int n_blocks, cudaStream_t s, int use_fast,
+                          int list = WARP_LIST_MAIN);
 template <int C>
 int occupancy_warp_c();
+template <int C>
+cudaError_t launch_warp16_c(const DevBatch *d_batch, int n_blocks, cudaStream_t s, int use_fast);
+template <int C>
+int occupancy_warp16_c();
 cudaError_t launch_plain_kernel(const DevBatch *d_batch, int64_t n_blocks, int32_t w_max,
                                 int use_wide_list, cudaStream_t s);
 int plain_kernel_max_w();

@@ -327,17 +327,21 @@ __device__ __forceinline__ bool warp_takes(const DevBatch &B, int32_t pair) {
 
 template <int C>
 __global__ void __launch_bounds__(WARP_BLOCK_THREADS)
-warp_align_kernel(const DevBatch *__restrict__ d_batch, int32_t use_fast) {
+warp_align_kernel(const DevBatch *__restrict__ d_batch, int32_t use_fast, int32_t list) {
     const DevBatch B = *d_batch;
     const int lane = threadIdx.x & 31;
-    const bool sorted = B.order != nullptr;
-    const int64_t n_work = sorted ? (int64_t)B.counters[CTR_NWARP] : B.n_pairs;
+    const bool ovf = list == WARP_LIST_OVERFLOW;
+    const bool sorted = ovf || B.order != nullptr;
+    const int32_t *items = ovf ? B.ovf_list : B.order;
+    int32_t *head = &B.counters[ovf ? CTR_OVF_HEAD : CTR_HEAD];
+    const int64_t n_work = ovf ? (int64_t)B.counters[CTR_NOVF]
+                               : (sorted ? (int64_t)B.counters[CTR_NWARP] : B.n_pairs);
     for (;;) {
         int32_t k = 0;
-        if (lane == 0) k = atomicAdd(&B.counters[CTR_HEAD], 1);
+        if (lane == 0) k = atomicAdd(head, 1);
         k = __shfl_sync(FULL, k, 0);
         if (k >= n_work) break;
-        const int32_t pair = sorted ? B.order[k] : k;
+        const int32_t pair = sorted ? items[k] : k;
         if (!sorted && (!pair_valid(B, pair) || !warp_takes(B, pair))) continue;
         WarpPair<C> wp;
         wp.run(B, pair, lane, use_fast != 0);
@@ -345,8 +349,9 @@ warp_align_kernel(const DevBatch *__restrict__ d_batch, int32_t use_fast) {
 }
 
 template <int C>
-cudaError_t launch_warp_c(const DevBatch *d_batch, int n_blocks, cudaStream_t s, int use_fast) {
-    warp_align_kernel<C><<<n_blocks, WARP_BLOCK_THREADS, 0, s>>>(d_batch, use_fast);
+cudaError_t launch_warp_c(const DevBatch *d_batch, int n_blocks, cudaStream_t s, int use_fast,
+                          int list) {
+    warp_align_kernel<C><<<n_blocks, WARP_BLOCK_THREADS, 0, s>>>(d_batch, use_fast, list);
     return cudaGetLastError();
 }
 

@@ -1,0 +1,563 @@
+// Batched persistent kernel on 16-bit packed lanes: one warp aligns one pair,
+// two band slots per 32-bit register, so one integer instruction updates two
+// cells of the anti-diagonal.
+//
+// Frame.  Anti-diagonal r holds the band cells t in [ceil((r-w)/2),
+// floor((r+w)/2)].  This kernel numbers them by the slot j = t - B(r) with
+// B(r) = floor((r - w) / 2):
+//   (r - w) even: slots 0..w are band cells; E comes from slot j of r-1,
+//                 F from slot j+1 of r-1, and the target window slides;
+//   (r - w) odd:  slots 1..w are band cells (slot 0 is t - q = -w-1); E comes
+//                 from slot j-1, F from slot j, and the query window slides;
+//   the diagonal predecessor is always the same slot two anti-diagonals back.
+// So the only slot outside the band inside [0, w] is slot 0 on odd
+// anti-diagonals, which belongs to lane 0 at a fixed place.
+//
+// Packing: register p of a lane holds slot j0+p in its low half and slot
+// j0+p+P in its high half (P = C/2).  Scores are stored as unsigned 16-bit
+// values u = v - base + OFF with a per-warp int32 base:
+//   - NEG (0x1000) stands for minus infinity;
+//   - D = the largest change one anti-diagonal can make (max of a, b, q+e,
+//     q2+e2).  At most every K anti-diagonals the warp rebases: base moves to
+//     the current anti-diagonal maximum (stored at OFF) and the warp checks,
+//     exactly, that every score of a band cell is at least (K+3)D above NEG.
+//     Between rebases scores then stay in [NEG + 2D, OFF + (K+1)D], clear of
+//     NEG and of 0xFFFF.  A pair that fails the check (a score spread of more
+//     than ~45,000 inside the band) is handed to the int32 kernel, which
+//     recomputes it from the start; no 16-bit result is written for it.
+//   - Real scores never come near 0 or 0xFFFF, so packed 32-bit adds and
+//     subtracts never carry or borrow across the two halves (a borrow out of a
+//     slot beyond the band can only reach the high half, which is then beyond
+//     the band as well).
+//
+// Per cell the bulk step issues about ten instructions: a bitwise mux picks
+// the substitution score from the mismatch bit (replicated by prmt), one
+// add-max and three 16x2 max form H, and each of the four gap states is one
+// add plus one 16x2 max.  Slots outside the band keep their outgoing gap
+// states at NEG through a per-slot mask, so nothing flows back into the band.
+// The registers are updated in place: F-from-j+1 steps walk the registers
+// upwards and E-from-j-1 steps downwards, so every old value is read before it
+// is overwritten and no copies are needed.
+#pragma once
+
+#include <climits>
+
+#include "kernel_warp.cuh"
+
+namespace agatha {
+
+constexpr uint32_t U_NEG = 0x1000u;     // minus infinity of the 16-bit lanes
+constexpr int32_t U_K = 128;            // anti-diagonals between rebases, at most
+
+__device__ __forceinline__ uint32_t prmt(uint32_t a, uint32_t b, uint32_t sel) {
+    uint32_t d;
+    asm("prmt.b32 %0, %1, %2, %3;" : "=r"(d) : "r"(a), "r"(b), "r"(sel));
+    return d;
+}
+
+// bits of x where m is set, bits of y elsewhere
+__device__ __forceinline__ uint32_t mux(uint32_t m, uint32_t x, uint32_t y) {
+    return (m & x) | (~m & y);
+}
+
+__host__ __device__ inline int32_t step_change_max(const DevParams &p) {
+    int32_t d = p.a > p.b ? p.a : p.b;
+    d = d > p.q + p.e ? d : p.q + p.e;
+    d = d > p.q2 + p.e2 ? d : p.q2 + p.e2;
+    return d > 0 ? d : 1;
+}
+
+template <int C>
+struct WarpPair16 {
+    static_assert(C == 8 || C == 16, "16-bit lanes use 8 or 16 slots per lane");
+    static constexpr int P = C / 2;
+
+    const uint32_t *tp, *qp;
+    int64_t tw, qw, toff, qoff;
+    int32_t tlen, qlen, w, last_r, lane, j0;
+    DevParams prm;
+    int32_t oe, oe2;
+    // packed band state: H of the last two anti-diagonals, gap states leaving
+    // the last one (Eo: to (t+1,q), Fo: to (t,q+1), E2o/F2o the second piece)
+    uint32_t H1[P], H2[P], Eo[P], E2o[P], Fo[P], F2o[P];
+    uint32_t DM[P];        // 0xFFFF halves: slot beyond the band (j > w)
+    uint32_t DM0odd;       // DM[0] plus slot 0 of lane 0 (outside on odd anti-diagonals)
+    // base windows (2 bits per slot): Tw field jl = T[B + j0 + jl],
+    // Qw field jl = Q[r - B - j0 - jl]
+    uint32_t Tw, Qw, Tpf, Qpf;
+    int32_t tcnt, qcnt;
+    int64_t tpos, qpos;
+    // relative scores
+    int32_t base, Dp, LOWCHK, OFF, since;
+    bool ovf;
+    // packed constants
+    uint32_t A2, NB2, OEp, DOEp, Ep, E2p, NEGp, L0LO, L31HI;
+    // bookkeeping (uniform across the warp)
+    int32_t gmax, gt, gq, mqe, mqe_t, mte, mte_q, gscore;
+    int64_t cells;
+    int32_t zdropped;
+
+    __device__ __forceinline__ int32_t to_true(int32_t u) const { return u - OFF + base; }
+    __device__ __forceinline__ int32_t to_u(int32_t v) const { return v - base + OFF; }
+    __device__ __forceinline__ int32_t frame(int32_t r) const { return floor_div2(r - w); }
+
+    // ------------------------------------------------------------ windows
+    __device__ __forceinline__ void init_windows(int32_t r) {
+        const int32_t B = frame(r);
+        const int64_t tb = (int64_t)B + j0;
+        const int64_t qb = (int64_t)r - B - j0;
+        const uint32_t mask = C == 16 ? 0xffffffffu : ((1u << (2 * C)) - 1);
+        Tw = load16(tp, tw, toff + tb) & mask;
+        Qw = rev2_32(load16(qp, qw, qoff + qb - C + 1)) >> (2 * (16 - C));
+        tpos = tb + C;
+        qpos = qb + 1;
+        Tpf = load16(tp, tw, toff + tpos);
+        Qpf = load16(qp, qw, qoff + qpos);
+        tpos += 16;
+        qpos += 16;
+        tcnt = 16;
+        qcnt = 16;
+    }
+    __device__ __forceinline__ void shift_t() {
+        Tw = (Tw >> 2) | ((Tpf & 3u) << (2 * C - 2));
+        Tpf >>= 2;
+        if (--tcnt == 0) { Tpf = load16(tp, tw, toff + tpos); tpos += 16; tcnt = 16; }
+    }
+    __device__ __forceinline__ void shift_q() {
+        const uint32_t mask = C == 16 ? 0xffffffffu : ((1u << (2 * C)) - 1);
+        Qw = ((Qw << 2) | (Qpf & 3u)) & mask;
+        Qpf >>= 2;
+        if (--qcnt == 0) { Qpf = load16(qp, qw, qoff + qpos); qpos += 16; qcnt = 16; }
+    }
+    // windows of anti-diagonal r from those of r-1
+    __device__ __forceinline__ void advance(int32_t r) {
+        if ((r - w) & 1) shift_q(); else shift_t();
+    }
+    // mismatch bit of slot jl at bit 2*jl
+    __device__ __forceinline__ uint32_t mismatch_bits() const {
+        const uint32_t x = Tw ^ Qw;
+        return (x | (x >> 1)) & 0x55555555u;
+    }
+    // the same bits with low-half slots p at bit 2p and high-half slots p+P at 16+2p
+    __device__ __forceinline__ uint32_t packed_mismatch() const {
+        const uint32_t nm = mismatch_bits();
+        if constexpr (C == 16) return nm;
+        else return (nm & 0xffu) | ((nm & 0xff00u) << 8);
+    }
+
+    // ------------------------------------------------------- Eq. 4-7 test
+    __device__ __forceinline__ bool max_and_zdrop(int32_t m, int32_t tstar, int32_t r) {
+        const int32_t qstar = r - tstar;
+        if (m > gmax) {
+            gmax = m; gt = tstar; gq = qstar;
+            return false;
+        }
+        if (tstar >= gt && qstar >= gq && prm.zdrop >= 0) {
+            int32_t l = (tstar - gt) - (qstar - gq);
+            l = l < 0 ? -l : l;
+            if (gmax - m > prm.zdrop + l * prm.e2) return true;
+        }
+        return false;
+    }
+
+    template <int JL>
+    __device__ __forceinline__ static int32_t half(const uint32_t (&a)[P]) {
+        if constexpr (JL < P) return (int32_t)(a[JL] & 0xffffu);
+        else return (int32_t)(a[JL - P] >> 16);
+    }
+
+    // --------------------------------------------------------- masked step
+    // One cell in int32 arithmetic on u values, every edge case handled.
+    // d = 1 on odd anti-diagonals (E from j-1, F from j), 0 on even ones.
+    template <int JL>
+    __device__ __forceinline__ void masked_cell(int32_t r, int32_t B, int32_t d, uint32_t nm,
+                                                int32_t eL, int32_t e2L, int32_t fR, int32_t f2R,
+                                                int32_t &oH, int32_t &oE, int32_t &oE2,
+                                                int32_t &oF, int32_t &oF2, int32_t &best,
+                                                int32_t &best_j, int32_t &te_c, int32_t &qe_c) {
+        const int32_t t = B + j0 + JL, q = r - t;
+        int32_t Ein, E2in, Fin, F2in;
+        if constexpr (JL == 0) {
+            Ein = d ? eL : half<0>(Eo);
+            E2in = d ? e2L : half<0>(E2o);
+        } else {
+            Ein = d ? half<JL - 1>(Eo) : half<JL>(Eo);
+            E2in = d ? half<JL - 1>(E2o) : half<JL>(E2o);
+        }
+        if constexpr (JL == C - 1) {
+            Fin = d ? half<JL>(Fo) : fR;
+            F2in = d ? half<JL>(F2o) : f2R;
+        } else {
+            Fin = d ? half<JL>(Fo) : half<JL + 1>(Fo);
+            F2in = d ? half<JL>(F2o) : half<JL + 1>(F2o);
+        }
+        const int32_t s = ((nm >> (2 * JL)) & 1u) ? -prm.b : prm.a;
+        int32_t H = max(max(half<JL>(H2) + s, Ein), max(max(Fin, E2in), F2in));
+        int32_t ne = max(H - oe, Ein - prm.e), nf = max(H - oe, Fin - prm.e);
+        int32_t ne2 = max(H - oe2, E2in - prm.e2), nf2 = max(H - oe2, F2in - prm.e2);
+        const int32_t k = t - q;
+        const bool real = t >= 0 && q >= 0 && t < tlen && q < qlen && k <= w && -k <= w;
+        if (real) {
+            if (H < (int32_t)U_NEG + 2 * Dp || H > 0xffff - Dp) ovf = true;
+            if (H > best) { best = H; best_j = JL; }
+            if (t == tlen - 1) te_c = H;
+            if (q == qlen - 1) qe_c = H;
+        } else {
+            const bool virt = (t == -1 && q >= -1 && q < qlen) || (q == -1 && t >= 0 && t < tlen);
+            if (virt) {
+                const int32_t v = (t == -1 && q == -1) ? 0 : -gap_cost(prm, (t == -1 ? q : t) + 1);
+                H = to_u(v);
+                if (H < (int32_t)U_NEG + 2 * Dp || H > 0xffff - Dp) ovf = true;
+                ne = nf = H - oe;
+                ne2 = nf2 = H - oe2;
+            } else {
+                H = ne = nf = ne2 = nf2 = (int32_t)U_NEG;
+            }
+        }
+        oH = H; oE = ne; oE2 = ne2; oF = nf; oF2 = nf2;
+    }
+
+    template <int PP>
+    __device__ __forceinline__ void masked_pair(int32_t r, int32_t B, int32_t d, uint32_t nm,
+                                                int32_t eL, int32_t e2L, int32_t fR, int32_t f2R,
+                                                uint32_t (&nH)[P], uint32_t (&nE)[P],
+                                                uint32_t (&nE2)[P], uint32_t (&nF)[P],
+                                                uint32_t (&nF2)[P], int32_t &lo_best,
+                                                int32_t &lo_j, int32_t &hi_best, int32_t &hi_j,
+                                                int32_t &te_c, int32_t &qe_c) {
+        int32_t h0, e0, e20, f0, f20, h1, e1, e21, f1, f21;
+        masked_cell<PP>(r, B, d, nm, eL, e2L, fR, f2R, h0, e0, e20, f0, f20, lo_best, lo_j, te_c, qe_c);
+        masked_cell<PP + P>(r, B, d, nm, eL, e2L, fR, f2R, h1, e1, e21, f1, f21, hi_best, hi_j, te_c,
+                            qe_c);
+        nH[PP] = (uint32_t)(h0 & 0xffff) | ((uint32_t)(h1 & 0xffff) << 16);
+        nE[PP] = (uint32_t)(e0 & 0xffff) | ((uint32_t)(e1 & 0xffff) << 16);
+        nE2[PP] = (uint32_t)(e20 & 0xffff) | ((uint32_t)(e21 & 0xffff) << 16);
+        nF[PP] = (uint32_t)(f0 & 0xffff) | ((uint32_t)(f1 & 0xffff) << 16);
+        nF2[PP] = (uint32_t)(f20 & 0xffff) | ((uint32_t)(f21 & 0xffff) << 16);
+        if constexpr (PP + 1 < P)
+            masked_pair<PP + 1>(r, B, d, nm, eL, e2L, fR, f2R, nH, nE, nE2, nF, nF2, lo_best, lo_j,
+                                hi_best, hi_j, te_c, qe_c);
+    }
+
+    __device__ __forceinline__ bool masked_step(int32_t r) {
+        const int32_t B = frame(r);
+        const int32_t d = (r - w) & 1;
+        if (r >= 0) {
+            const int32_t st = max(max(0, r - qlen + 1), ceil_div2(r - w));
+            const int32_t en = min(min(tlen - 1, r), floor_div2(r + w));
+            if (st > en) { zdropped = 1; return true; }      // the band left the table
+            cells += en - st + 1;
+        }
+        const uint32_t eLp = __shfl_up_sync(FULL, Eo[P - 1], 1);
+        const uint32_t e2Lp = __shfl_up_sync(FULL, E2o[P - 1], 1);
+        const uint32_t fRp = __shfl_down_sync(FULL, Fo[0], 1);
+        const uint32_t f2Rp = __shfl_down_sync(FULL, F2o[0], 1);
+        int32_t eL = (int32_t)(eLp >> 16), e2L = (int32_t)(e2Lp >> 16);
+        int32_t fR = (int32_t)(fRp & 0xffffu), f2R = (int32_t)(f2Rp & 0xffffu);
+        // slot 0 of lane 0 takes E from slot -1 only on odd anti-diagonals,
+        // where it is outside the band or a virtual cell: its input never counts
+        if (lane == 0) eL = e2L = (int32_t)U_NEG;
+        if (lane == 31) {
+            // F of the last slot on even anti-diagonals: slot 32C of r-1, the
+            // virtual column cell (t, -1) when q == -1 there, else outside
+            const int32_t ts = frame(r - 1) + 32 * C, qs = r - 1 - ts;
+            if (qs == -1 && ts >= 0 && ts < tlen) {
+                const int32_t v = to_u(-gap_cost(prm, ts + 1));
+                if (v < (int32_t)U_NEG + 2 * Dp || v > 0xffff - Dp) ovf = true;
+                fR = v - oe; f2R = v - oe2;
+            } else {
+                fR = f2R = (int32_t)U_NEG;
+            }
+        }
+        const uint32_t nm = mismatch_bits();
+        uint32_t nH[P], nE[P], nE2[P], nF[P], nF2[P];
+        int32_t lo_best = INT_MIN, lo_j = -1, hi_best = INT_MIN, hi_j = -1;
+        int32_t te_c = INT_MIN, qe_c = INT_MIN;
+        masked_pair<0>(r, B, d, nm, eL, e2L, fR, f2R, nH, nE, nE2, nF, nF2, lo_best, lo_j, hi_best,
+                       hi_j, te_c, qe_c);
+#pragma unroll
+        for (int p = 0; p < P; ++p) {
+            H2[p] = H1[p]; H1[p] = nH[p];
+            Eo[p] = nE[p]; E2o[p] = nE2[p]; Fo[p] = nF[p]; F2o[p] = nF2[p];
+        }
+        if (__any_sync(FULL, ovf)) { ovf = true; return true; }
+        if (r < 0) return false;
+        const int32_t te_v = __reduce_max_sync(FULL, te_c);
+        if (te_v != INT_MIN && to_true(te_v) > mte) { mte = to_true(te_v); mte_q = r - (tlen - 1); }
+        const int32_t qe_v = __reduce_max_sync(FULL, qe_c);
+        if (qe_v != INT_MIN && to_true(qe_v) > mqe) { mqe = to_true(qe_v); mqe_t = r - (qlen - 1); }
+        // lowest-index maximum of the lane: low halves hold the smaller slots
+        const int32_t lm = lo_best >= hi_best ? lo_best : hi_best;
+        const int32_t li = lo_best >= hi_best ? lo_j : hi_j;
+        const int32_t m = __reduce_max_sync(FULL, lm);
+        const unsigned ball = __ballot_sync(FULL, lm == m && li >= 0);
+        const int src = __ffs(ball) - 1;
+        const int32_t lj = __shfl_sync(FULL, li, src);
+        if (max_and_zdrop(to_true(m), B + src * C + lj, r)) { zdropped = 1; return true; }
+        if (r == last_r && te_v != INT_MIN && (r - (tlen - 1)) == qlen - 1) gscore = to_true(te_v);
+        if (++since >= U_K - 2) rebase(m, r);
+        return ovf;
+    }
+
+    // ----------------------------------------------------------- bulk step
+    // One bulk anti-diagonal on the packed registers, in place: Hd holds H of
+    // r-2 on entry and H of r on exit, the gap arrays hold the states leaving
+    // r-1 on entry and r on exit.  ODD: (r - w) odd.  Applies the
+    // termination rule to the anti-diagonal; returns true to stop.
+    template <bool ODD>
+    __device__ __forceinline__ bool cell_step(int32_t r, uint32_t (&Hd)[P]) {
+        const int32_t B = frame(r);
+        uint32_t edge, edge2;
+        if constexpr (ODD) {
+            // E of slot 0 from the left lane's last slot (high half of its last register)
+            const uint32_t eL = __shfl_up_sync(FULL, Eo[P - 1], 1);
+            const uint32_t e2L = __shfl_up_sync(FULL, E2o[P - 1], 1);
+            edge = mux(L0LO, NEGp, prmt(eL, Eo[P - 1], 0x5432));
+            edge2 = mux(L0LO, NEGp, prmt(e2L, E2o[P - 1], 0x5432));
+        } else {
+            // F of the last slot from the right lane's first slot (low half of its register 0)
+            const uint32_t fR = __shfl_down_sync(FULL, Fo[0], 1);
+            const uint32_t f2R = __shfl_down_sync(FULL, F2o[0], 1);
+            edge = mux(L31HI, NEGp, prmt(Fo[0], fR, 0x5432));
+            edge2 = mux(L31HI, NEGp, prmt(F2o[0], f2R, 0x5432));
+        }
+        const uint32_t comb = packed_mismatch();
+        uint32_t lmax = 0;
+#pragma unroll
+        for (int i = 0; i < P; ++i) {
+            const int p = ODD ? P - 1 - i : i;       // read every old value before overwriting it
+            uint32_t Ein, E2in, Fin, F2in;
+            if constexpr (ODD) {
+                Ein = p ? Eo[p - 1] : edge;
+                E2in = p ? E2o[p - 1] : edge2;
+                Fin = Fo[p];
+                F2in = F2o[p];
+            } else {
+                Ein = Eo[p];
+                E2in = E2o[p];
+                Fin = p < P - 1 ? Fo[p + 1] : edge;
+                F2in = p < P - 1 ? F2o[p + 1] : edge2;
+            }
+            // substitution: mismatch bits of both halves replicated to 0xFFFF masks
+            const uint32_t mm = prmt(comb << (15 - 2 * p), 0, 0xbb99);
+            const uint32_t s2 = mux(mm, NB2, A2);
+            uint32_t H = __viaddmax_u16x2(Hd[p], s2, Ein);
+            H = __vmaxu2(H, Fin);
+            H = __vmaxu2(H, __vmaxu2(E2in, F2in));
+            const uint32_t dead = (ODD && p == 0) ? DM0odd : DM[p];
+            const uint32_t hoe = mux(dead, NEGp, H - OEp);
+            const uint32_t hoe2 = hoe - DOEp;
+            Eo[p] = __vmaxu2(Ein - Ep, hoe);
+            Fo[p] = __vmaxu2(Fin - Ep, hoe);
+            E2o[p] = __vmaxu2(E2in - E2p, hoe2);
+            F2o[p] = __vmaxu2(F2in - E2p, hoe2);
+            Hd[p] = H;
+            lmax = __vmaxu2(lmax, hoe);
+        }
+        // anti-diagonal maximum (of H - q - e, in u); its position is only
+        // needed when it is a new global maximum or a possible Z-drop
+        const int32_t lm = (int32_t)max(lmax & 0xffffu, lmax >> 16);
+        const int32_t m = __reduce_max_sync(FULL, lm);
+        const int32_t mt = to_true(m + oe);
+        cells += w + 1 - (ODD ? 1 : 0);
+        if (mt > gmax || (prm.zdrop >= 0 && gmax - mt > prm.zdrop)) {
+            // lowest slot of the first lane holding the maximum: bit p / 16+p
+            // of `ne` is set where the low / high half of register p is not it
+            const unsigned ball = __ballot_sync(FULL, lm == m);
+            const int src = __ffs(ball) - 1;
+            const uint32_t mh2 = (uint32_t)(m + oe) * 0x10001u;
+            uint32_t ne = 0;
+#pragma unroll
+            for (int p = 0; p < P; ++p) {
+                const uint32_t dead = (ODD && p == 0) ? DM0odd : DM[p];
+                ne += __vminu2((Hd[p] ^ mh2) | dead, 0x10001u) << p;
+            }
+            const uint32_t eq = ~ne & ((((1u << P) - 1) << 16) | ((1u << P) - 1));
+            const uint32_t lo_eq = eq & 0xffffu, hi_eq = eq >> 16;
+            const int32_t jl = lo_eq ? __ffs(lo_eq) - 1 : P + __ffs(hi_eq) - 1;
+            const int32_t lj = __shfl_sync(FULL, jl, src);
+            if (max_and_zdrop(mt, B + src * C + lj, r)) { zdropped = 1; return true; }
+        }
+        last_m = m + oe;
+        return false;
+    }
+
+    // Bulk anti-diagonals r ((r - w) even) and r+1.  On entry H2 = H(r-2),
+    // H1 = H(r-1), gap states leave r-1; on exit the same for r+1 (H2 ends up
+    // holding H(r) and H1 H(r+1), the canonical order).  Returns 0 to go on,
+    // else k+1 when the extension stopped on r+k.
+    __device__ __forceinline__ int fast_pair(int32_t r) {
+        shift_t();
+        if (cell_step<false>(r, H2)) return 1;
+        shift_q();
+        if (cell_step<true>(r + 1, H1)) return 2;
+        since += 2;
+        if (since >= U_K - 2) {
+            rebase(last_m, r + 1);
+            if (ovf) return 2;
+        }
+        return 0;
+    }
+    int32_t last_m;
+
+    // ---------------------------------------------------------------- rebase
+    // Move base so that the anti-diagonal maximum m_u is stored at OFF; check
+    // that every band score keeps (K+3)D of headroom above NEG; reset minus
+    // infinity (anything at most NEG) and slots outside the band to NEG.
+    __device__ __forceinline__ void rebase_reg(uint32_t &x, uint32_t dm, int32_t delta, int32_t low) {
+        int32_t lo = (int32_t)(x & 0xffffu), hi = (int32_t)(x >> 16);
+        const bool dlo = dm & 1u, dhi = dm >> 31;
+        if (dlo || lo <= (int32_t)U_NEG) lo = (int32_t)U_NEG;
+        else { if (lo < low) ovf = true; lo = min(max(lo - delta, (int32_t)U_NEG + 1), 0xffff); }
+        if (dhi || hi <= (int32_t)U_NEG) hi = (int32_t)U_NEG;
+        else { if (hi < low) ovf = true; hi = min(max(hi - delta, (int32_t)U_NEG + 1), 0xffff); }
+        x = (uint32_t)lo | ((uint32_t)hi << 16);
+    }
+    // H1 = H(r), H2 = H(r-1), gap states leave r
+    __device__ __forceinline__ void rebase(int32_t m_u, int32_t r) {
+        since = 0;
+        const int32_t delta = m_u - OFF;
+        const int32_t low = LOWCHK - Dp + delta;
+        const bool odd = ((r - w) & 1) != 0;
+#pragma unroll
+        for (int p = 0; p < P; ++p) {
+            const uint32_t dm_odd = p == 0 ? DM0odd : DM[p];
+            const uint32_t dm_r = odd ? dm_odd : DM[p];       // slots of anti-diagonal r
+            const uint32_t dm_r1 = odd ? DM[p] : dm_odd;      // slots of r-1
+            rebase_reg(H1[p], dm_r, delta, low);
+            rebase_reg(H2[p], dm_r1, delta, low);
+            rebase_reg(Eo[p], dm_r, delta, low);
+            rebase_reg(E2o[p], dm_r, delta, low);
+            rebase_reg(Fo[p], dm_r, delta, low);
+            rebase_reg(F2o[p], dm_r, delta, low);
+        }
+        base += delta;
+        if (__any_sync(FULL, ovf)) ovf = true;
+    }
+
+    // ------------------------------------------------------------------ pair
+    // Returns false if the pair must be recomputed with int32 lanes.
+    __device__ __forceinline__ bool run(const DevBatch &Bt, int32_t pair, int32_t lane_, bool use_fast) {
+        prm = Bt.params;
+        lane = lane_;
+        tp = Bt.t_packed; qp = Bt.q_packed; tw = Bt.t_words; qw = Bt.q_words;
+        tlen = Bt.t_len[pair]; qlen = Bt.q_len[pair];
+        toff = Bt.t_off[pair]; qoff = Bt.q_off[pair];
+        agatha_result *out = Bt.out + pair;
+        if (tlen <= 0 || qlen <= 0) {
+            if (lane == 0) write_empty_result(out);
+            return true;
+        }
+        w = effective_w(prm.w, tlen, qlen);
+        oe = prm.q + prm.e; oe2 = prm.q2 + prm.e2;
+        j0 = lane * C;
+        last_r = tlen + qlen - 2;
+        Dp = step_change_max(prm);
+        LOWCHK = (int32_t)U_NEG + (U_K + 3) * Dp;
+        OFF = 0xffff - (U_K + 3) * Dp;
+        base = 0;
+        since = 0;
+        ovf = false;
+        A2 = ((uint32_t)prm.a & 0xffffu) * 0x10001u;
+        NB2 = ((uint32_t)(-prm.b) & 0xffffu) * 0x10001u;
+        OEp = (uint32_t)oe * 0x10001u;
+        DOEp = (uint32_t)(oe2 - oe) * 0x10001u;
+        Ep = (uint32_t)prm.e * 0x10001u;
+        E2p = (uint32_t)prm.e2 * 0x10001u;
+        NEGp = U_NEG * 0x10001u;
+        L0LO = lane == 0 ? 0x0000ffffu : 0u;
+        L31HI = lane == 31 ? 0xffff0000u : 0u;
+#pragma unroll
+        for (int p = 0; p < P; ++p) {
+            const int32_t jlo = j0 + p, jhi = j0 + p + P;
+            DM[p] = (jlo > w ? 0x0000ffffu : 0u) | (jhi > w ? 0xffff0000u : 0u);
+            H1[p] = H2[p] = Eo[p] = E2o[p] = Fo[p] = F2o[p] = NEGp;
+        }
+        DM0odd = DM[0] | L0LO;
+        gmax = 0; gt = -1; gq = -1;
+        mqe = K_NEG_OUT; mqe_t = -1; mte = K_NEG_OUT; mte_q = -1; gscore = K_NEG_OUT;
+        cells = 0; zdropped = 0;
+
+        int32_t r = -2;
+        init_windows(r);
+        bool stop = masked_step(r);
+        const int32_t head_end = min(last_r, w + 1);
+        while (!stop && r < head_end) {
+            ++r;
+            advance(r);
+            stop = masked_step(r);
+        }
+        // bulk: pairs starting at r = w + 2 ((r - w) even) while every band cell
+        // of the pair is a real cell away from the last row and column
+        const int32_t L = min(tlen, qlen);
+        const int32_t bulk_last = 2 * L - 3 - w;
+        if (use_fast && !stop && r == w + 1) {
+            while (r + 2 <= bulk_last) {
+                const int st = fast_pair(r + 1);
+                if (st) {
+                    r += st;          // stopped (Z-drop or 16-bit overflow) on r+st
+                    stop = true;
+                    break;
+                }
+                r += 2;
+            }
+        }
+        while (!stop && r < last_r) {
+            ++r;
+            advance(r);
+            stop = masked_step(r);
+        }
+        if (ovf) return false;
+        if (lane == 0) {
+            agatha_result o;
+            o.max = gmax; o.te = gt; o.qe = gq;
+            o.gscore = gscore; o.mqe = mqe; o.mqe_t = mqe_t; o.mte = mte; o.mte_q = mte_q;
+            o.cells = cells;
+            o.zdropped = (uint8_t)zdropped;
+            o.reach_end = (uint8_t)(!zdropped && mqe != K_NEG_OUT && mqe + prm.end_bonus > gmax);
+            o.lane16 = 1;
+            for (int i = 0; i < 5; ++i) o.pad[i] = 0;
+            *out = o;
+        }
+        return true;
+    }
+};
+
+template <int C>
+__global__ void __launch_bounds__(WARP_BLOCK_THREADS, 3)
+warp16_align_kernel(const DevBatch *__restrict__ d_batch, int32_t use_fast) {
+    const DevBatch B = *d_batch;
+    const int lane = threadIdx.x & 31;
+    const bool sorted = B.order != nullptr;
+    const int64_t n_work = sorted ? (int64_t)B.counters[CTR_NWARP] : B.n_pairs;
+    for (;;) {
+        int32_t k = 0;
+        if (lane == 0) k = atomicAdd(&B.counters[CTR_HEAD], 1);
+        k = __shfl_sync(FULL, k, 0);
+        if (k >= n_work) break;
+        const int32_t pair = sorted ? B.order[k] : k;
+        if (!sorted && (!pair_valid(B, pair) || !warp_takes(B, pair))) continue;
+        WarpPair16<C> wp;
+        if (!wp.run(B, pair, lane, use_fast != 0) && lane == 0) {
+            const int32_t slot = atomicAdd(&B.counters[CTR_NOVF], 1);
+            B.ovf_list[slot] = pair;
+        }
+    }
+}
+
+template <int C>
+cudaError_t launch_warp16_c(const DevBatch *d_batch, int n_blocks, cudaStream_t s, int use_fast) {
+    warp16_align_kernel<C><<<n_blocks, WARP_BLOCK_THREADS, 0, s>>>(d_batch, use_fast);
+    return cudaGetLastError();
+}
+
+template <int C>
+int occupancy_warp16_c() {
+    int nb = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, warp16_align_kernel<C>,
+                                                      WARP_BLOCK_THREADS, 0) != cudaSuccess)
+        return 1;
+    return nb > 0 ? nb : 1;
+}
+
+}  // namespace agatha

@@ -2,6 +2,6 @@
 #include "kernel_warp.cuh"
 
 namespace agatha {
-template cudaError_t launch_warp_c<24>(const DevBatch *, int, cudaStream_t, int);
+template cudaError_t launch_warp_c<24>(const DevBatch *, int, cudaStream_t, int, int);
 template int occupancy_warp_c<24>();
 }  // namespace agatha

@@ -13,6 +13,7 @@
 #include <vector>
 
 #include "agatha_dev.cuh"
+#include "kernel_warp16.cuh"
 #include "runtime.h"
 
 using namespace agatha;
@@ -155,14 +156,30 @@ int pick_slots_per_lane(int32_t w) {
     return 32;
 }
 
-static cudaError_t launch_warp(int C, const DevBatch *d, int blocks, cudaStream_t s, int fast) {
+static cudaError_t launch_warp(int C, const DevBatch *d, int blocks, cudaStream_t s, int fast,
+                               int list) {
     switch (C) {
-        case 4: return launch_warp_c<4>(d, blocks, s, fast);
-        case 8: return launch_warp_c<8>(d, blocks, s, fast);
-        case 16: return launch_warp_c<16>(d, blocks, s, fast);
-        case 24: return launch_warp_c<24>(d, blocks, s, fast);
-        default: return launch_warp_c<32>(d, blocks, s, fast);
+        case 4: return launch_warp_c<4>(d, blocks, s, fast, list);
+        case 8: return launch_warp_c<8>(d, blocks, s, fast, list);
+        case 16: return launch_warp_c<16>(d, blocks, s, fast, list);
+        case 24: return launch_warp_c<24>(d, blocks, s, fast, list);
+        default: return launch_warp_c<32>(d, blocks, s, fast, list);
     }
+}
+
+static cudaError_t launch_warp16(int C, const DevBatch *d, int blocks, cudaStream_t s, int fast) {
+    return C == 8 ? launch_warp16_c<8>(d, blocks, s, fast) : launch_warp16_c<16>(d, blocks, s, fast);
+}
+
+int warp16_occupancy(int C) {
+    return C == 8 ? occupancy_warp16_c<8>() : occupancy_warp16_c<16>();
+}
+
+// Slots per lane of the 16-bit kernel for a band of half-width w (0: none).
+int pick_slots16(int32_t w) {
+    if (w <= 32 * 8 - 1) return 8;
+    if (w <= 32 * 16 - 1) return 16;
+    return 0;
 }
 
 int warp_occupancy(int C) {
@@ -192,7 +209,14 @@ static cudaError_t enqueue_part(agatha_ctx *ctx, const LaunchPlan &lp, int part,
         return launch_prep(ctx->d_desc, lp.n, lp.plain ? 0 : lp.sort, s, ctx->n_sm);
     }
     if (lp.plain) return launch_plain_kernel(ctx->d_desc, lp.plain_blocks, lp.plain_w, 0, s);
-    e = launch_warp(lp.C, ctx->d_desc, lp.warp_blocks, s, lp.fast);
+    if (lp.lane16) {
+        e = launch_warp16(lp.C16, ctx->d_desc, lp.warp16_blocks, s, lp.fast);
+        if (e != cudaSuccess) return e;
+        // pairs whose scores left the 16-bit range, recomputed on int32 lanes
+        e = launch_warp(lp.C, ctx->d_desc, lp.warp_blocks, s, lp.fast, WARP_LIST_OVERFLOW);
+    } else {
+        e = launch_warp(lp.C, ctx->d_desc, lp.warp_blocks, s, lp.fast, WARP_LIST_MAIN);
+    }
     if (e != cudaSuccess) return e;
     if (lp.wide_w > 0) e = launch_plain_kernel(ctx->d_desc, (int64_t)ctx->n_sm * 2, lp.wide_w, 1, s);
     return e;
@@ -248,6 +272,7 @@ int ensure_batch_buffers(agatha_ctx *ctx, int64_t n, int64_t q_words, int64_t t_
     }
     if ((rc = ctx->order.ensure(ctx, (size_t)n1 * 4))) return rc;
     if ((rc = ctx->wide_order.ensure(ctx, (size_t)n1 * 4))) return rc;
+    if ((rc = ctx->ovf_list.ensure(ctx, (size_t)n1 * 4))) return rc;
     return AGATHA_OK;
 }
 
@@ -280,6 +305,14 @@ int make_plan(agatha_ctx *ctx, const DevParams &p, const BatchShape &shape, uint
                          lp->wide_w, pmax);
     const int occ = warp_occupancy(lp->C);
     lp->warp_blocks = ctx->n_sm * occ;
+    // 16-bit packed lanes when the band fits and one anti-diagonal changes a
+    // score by at most 64 (see kernel_warp16.cuh)
+    lp->C16 = pick_slots16(shape.max_w_all);
+    lp->lane16 = !(flags & AGATHA_FORCE32) && lp->C16 > 0 && step_change_max(p) <= 64 && !lp->wide_w;
+    if (lp->lane16) {
+        lp->warp_w_max = 32 * lp->C16 - 1;
+        lp->warp16_blocks = ctx->n_sm * warp16_occupancy(lp->C16);
+    }
     lp->plain_w = 0;
     lp->plain_blocks = 0;
     return AGATHA_OK;
@@ -290,6 +323,7 @@ void fill_desc(agatha_ctx *ctx, DevBatch *d, const DevParams &p, const LaunchPla
     d->counters = (int32_t *)ctx->counters.ptr;
     d->wide_order = (int32_t *)ctx->wide_order.ptr;
     d->bucket_hist = (int64_t *)ctx->hist.ptr;
+    d->ovf_list = (int32_t *)ctx->ovf_list.ptr;
     d->params = p;
     d->warp_w_max = lp.plain ? INT32_MAX : lp.warp_w_max;
     d->pad = 0;
@@ -374,7 +408,7 @@ extern "C" void agatha_destroy(agatha_ctx *ctx) {
     for (auto &kv : ctx->graphs) cudaGraphExecDestroy(kv.second);
     ctx->graphs.clear();
     DevBuf *bufs[] = {&ctx->q_packed, &ctx->t_packed, &ctx->q_off, &ctx->t_off, &ctx->q_len,
-                      &ctx->t_len, &ctx->out, &ctx->order, &ctx->wide_order, &ctx->counters,
+                      &ctx->t_len, &ctx->out, &ctx->order, &ctx->wide_order, &ctx->ovf_list, &ctx->counters,
                       &ctx->hist, &ctx->desc};
     for (DevBuf *b : bufs) b->release();
     if (ctx->ev_k0) cudaEventDestroy(ctx->ev_k0);

@@ -42,11 +42,12 @@ struct LaunchPlan {
     int C = 16;
     int32_t warp_w_max = 0;
     int warp_blocks = 0;
+    int lane16 = 0, C16 = 0, warp16_blocks = 0;
     int32_t wide_w = 0;         // > 0: pairs wider than the warp kernel exist
     int32_t plain_w = 0;
     int64_t plain_blocks = 0;
     std::tuple<int, int, int, int, int32_t, int> key() const {
-        return std::make_tuple(plain, C, sort, fast, wide_w, warp_blocks);
+        return std::make_tuple(plain, C + 100 * C16 * lane16, sort, fast, wide_w, warp_blocks);
     }
 };
 
@@ -73,7 +74,7 @@ struct agatha_ctx {
     std::mutex err_mu;
     std::string last_error, last_error_copy;
     agatha::DevBuf q_packed, t_packed, q_off, t_off, q_len, t_len, out, order, wide_order,
-        counters, hist, desc;
+        ovf_list, counters, hist, desc;
     agatha::DevBatch *d_desc = nullptr;
     agatha::DevBatch *h_desc = nullptr;
     int32_t *h_counters = nullptr;

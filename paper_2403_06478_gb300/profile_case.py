@@ -22,10 +22,18 @@ def main():
     ap.add_argument("--workload", default="ont")
     ap.add_argument("--pairs", type=int, default=2000)
     ap.add_argument("--repeat", type=int, default=2)
+    ap.add_argument("--length", type=int, default=20000, help="pair length of --workload identical")
     ap.add_argument("--path", default="batched", choices=sorted(FLAGS))
     args = ap.parse_args()
     B.build()
-    batch = W.make_config(args.workload, n_pairs=args.pairs)
+    if args.workload == "identical":
+        # long identical pairs: every anti-diagonal after the first w+2 is a bulk step
+        import numpy as np
+        rng = np.random.default_rng(5)
+        xs = [rng.integers(0, 4, args.length).astype(np.uint8) for _ in range(args.pairs)]
+        batch = W.from_pairs(xs, [x.copy() for x in xs], W.ONT_SCORING, name="identical")
+    else:
+        batch = W.make_config(args.workload, n_pairs=args.pairs)
     pb = A.pack_batch(batch)
     with A.Context(0) as ctx:
         for _ in range(args.repeat):

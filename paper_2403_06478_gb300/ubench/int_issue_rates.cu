@@ -27,6 +27,27 @@ __device__ __forceinline__ int op(int a, int b, int c) {
     if constexpr (OP == 13) return max(max(a, b), c);             // two IMNMX or one 3-input
     if constexpr (OP == 14) return __shfl_xor_sync(0xffffffffu, a, 1) + b;
     if constexpr (OP == 15) return a * b + c;                     // IMAD
+    if constexpr (OP == 16) return (int)__vmaxu2((unsigned)a, (unsigned)b);
+    if constexpr (OP == 17) {                                     // prmt sign-replicate
+        unsigned d;
+        asm("prmt.b32 %0, %1, %2, %3;" : "=r"(d) : "r"(a), "r"(b), "r"(0xbb99));
+        return (int)d;
+    }
+    if constexpr (OP == 18) return (int)__viaddmin_u16x2((unsigned)a, (unsigned)b, (unsigned)c);
+    if constexpr (OP == 19) return (int)__vminu2((unsigned)a, (unsigned)b);
+    if constexpr (OP == 20) return (a << 3) + b;                  // shift + add (LEA)
+    if constexpr (OP == 21) {                                     // one packed bulk cell
+        unsigned H = __viaddmax_u16x2((unsigned)a, (unsigned)b, (unsigned)c);
+        H = __vmaxu2(H, (unsigned)b ^ 7u);
+        H = __vmaxu2(H, __vmaxu2((unsigned)c ^ 3u, (unsigned)b ^ 5u));
+        unsigned hoe = H - 0x00060006u;
+        unsigned e1 = __vmaxu2((unsigned)b - 0x00020002u, hoe);
+        unsigned f1 = __vmaxu2((unsigned)c - 0x00020002u, hoe);
+        unsigned hoe2 = hoe - 0x00140014u;
+        unsigned e2 = __vmaxu2((unsigned)b - 0x00010001u, hoe2);
+        unsigned f2 = __vmaxu2((unsigned)c - 0x00010001u, hoe2);
+        return (int)(e1 ^ f1 ^ e2 ^ f2 ^ H);
+    }
     return a;
 }
 
@@ -93,6 +114,12 @@ int main() {
         run<9>("test+sel", nsm, threads, d_out, d_cyc);
         run<15>("imad", nsm, threads, d_out, d_cyc);
         run<14>("shfl+add", nsm, threads, d_out, d_cyc);
+        run<16>("vmaxu2", nsm, threads, d_out, d_cyc);
+        run<17>("prmt", nsm, threads, d_out, d_cyc);
+        run<18>("viaddmin_u16x2", nsm, threads, d_out, d_cyc);
+        run<19>("vminu2", nsm, threads, d_out, d_cyc);
+        run<20>("shl+add", nsm, threads, d_out, d_cyc);
+        run<21>("packed cell (x1)", nsm, threads, d_out, d_cyc);
     }
     cudaError_t e = cudaGetLastError();
     printf("status: %s\n", cudaGetErrorString(e));

@@ -21,6 +21,8 @@ PATHS = {
     "edge_only": A.AGATHA_EDGE_PATH_ONLY,
     "no_sort": A.AGATHA_NO_SORT,
     "no_graph": A.AGATHA_NO_GRAPH,
+    "force32": A.AGATHA_FORCE32,
+    "force32_edge": A.AGATHA_FORCE32 | A.AGATHA_EDGE_PATH_ONLY,
 }
 
 
@@ -92,9 +94,41 @@ def test_adversarial_pairs(ctx, si):
     scoring = ADVERSARIAL_SCORINGS[si]
     batch = _adversarial_batch(np.random.default_rng(100 + si), scoring)
     ref = O.align_batch(batch)
-    for path in ("batched", "plain", "edge_only"):
+    for path in ("batched", "plain", "edge_only", "force32"):
         got = A.agatha_align_batch(ctx, batch, flags=PATHS[path])
         _assert_same(got, ref, batch, f"adversarial[{si}]/{path}")
+
+
+def test_16bit_lanes_used_and_exact(ctx):
+    batch = W.make_config("ont", n_pairs=300)
+    got = A.agatha_align_batch(ctx, batch)
+    assert got["lane16"].mean() > 0.99          # w=500 and ONT scoring fit 16-bit lanes
+    ref = A.agatha_align_batch(ctx, batch, flags=A.AGATHA_FORCE32)
+    assert (ref["lane16"] == 0).all()
+    assert A.results_equal(got, ref).size == 0
+
+
+def test_16bit_overflow_hands_pairs_to_int32(ctx):
+    # identical sequences with a = b = 64 and a 1 + 63 l gap cost: on every
+    # anti-diagonal the band edge sits about 32*511 + gap(511) = 48.5k below the
+    # maximum, more spread than the 16-bit lanes keep at this step size (~44.7k),
+    # so these pairs must come back exact from the int32 recomputation
+    rng = np.random.default_rng(17)
+    scoring = W.Scoring(64, 64, 1, 63, 1, 63, 511, -1, 0)
+    qs, ts = [], []
+    for k in range(6):
+        x = rng.integers(0, 4, 2500 + 100 * k).astype(np.uint8)
+        qs.append(x)
+        ts.append(x.copy())
+    for k in range(6):                           # short pairs stay within 16 bits
+        x = rng.integers(0, 4, 250).astype(np.uint8)
+        qs.append(x)
+        ts.append(x.copy())
+    batch = W.from_pairs(qs, ts, scoring)
+    got = A.agatha_align_batch(ctx, batch)
+    _assert_same(got, O.align_batch(batch), batch, "overflow")
+    assert (got["lane16"][:6] == 0).all()         # recomputed on int32 lanes
+    assert (got["lane16"][6:] == 1).all()
 
 
 def test_empty_batch_and_empty_pairs(ctx):
