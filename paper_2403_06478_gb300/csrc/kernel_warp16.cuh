@@ -37,7 +37,8 @@
 // states at NEG through a per-slot mask, so nothing flows back into the band.
 // The registers are updated in place: F-from-j+1 steps walk the registers
 // upwards and E-from-j-1 steps downwards, so every old value is read before it
-// is overwritten and no copies are needed.
+// is overwritten and no copies are needed.  Anti-diagonals where the band meets
+// the table's edges run the same packed update followed by per-slot masks.
 #pragma once
 
 #include <climits>
@@ -77,9 +78,11 @@ struct WarpPair16 {
     int32_t tlen, qlen, w, last_r, lane, j0;
     DevParams prm;
     int32_t oe, oe2;
-    // packed band state: H of the last two anti-diagonals, gap states leaving
-    // the last one (Eo: to (t+1,q), Fo: to (t,q+1), E2o/F2o the second piece)
-    uint32_t H1[P], H2[P], Eo[P], E2o[P], Fo[P], F2o[P];
+    // packed band state.  H(r) overwrites H(r-2) in the array of its parity:
+    // Hev holds H of the last anti-diagonal with (r - w) even, Hod of the last
+    // odd one.  Gap states leaving the last anti-diagonal: Eo to (t+1,q), Fo
+    // to (t,q+1), E2o/F2o the same for the second gap piece.
+    uint32_t Hev[P], Hod[P], Eo[P], E2o[P], Fo[P], F2o[P];
     uint32_t DM[P];        // 0xFFFF halves: slot beyond the band (j > w)
     uint32_t DM0odd;       // DM[0] plus slot 0 of lane 0 (outside on odd anti-diagonals)
     // base windows (2 bits per slot): Tw field jl = T[B + j0 + jl],
@@ -88,7 +91,7 @@ struct WarpPair16 {
     int32_t tcnt, qcnt;
     int64_t tpos, qpos;
     // relative scores
-    int32_t base, Dp, LOWCHK, OFF, since;
+    int32_t base, Dp, LOWCHK, OFF, since, last_m;
     bool ovf;
     // packed constants
     uint32_t A2, NB2, OEp, DOEp, Ep, E2p, NEGp, L0LO, L31HI;
@@ -133,16 +136,29 @@ struct WarpPair16 {
     __device__ __forceinline__ void advance(int32_t r) {
         if ((r - w) & 1) shift_q(); else shift_t();
     }
-    // mismatch bit of slot jl at bit 2*jl
-    __device__ __forceinline__ uint32_t mismatch_bits() const {
-        const uint32_t x = Tw ^ Qw;
-        return (x | (x >> 1)) & 0x55555555u;
-    }
-    // the same bits with low-half slots p at bit 2p and high-half slots p+P at 16+2p
+    // mismatch bits: low-half slot p at bit 2p, high-half slot p+P at 16+2p
     __device__ __forceinline__ uint32_t packed_mismatch() const {
-        const uint32_t nm = mismatch_bits();
+        const uint32_t x = Tw ^ Qw;
+        const uint32_t nm = (x | (x >> 1)) & 0x55555555u;    // slot jl at bit 2*jl
         if constexpr (C == 16) return nm;
         else return (nm & 0xffu) | ((nm & 0xff00u) << 8);
+    }
+    // 0xFFFF halves of register p from lane bits (low half p at bit p, high at 16+p)
+    template <int PP>
+    __device__ __forceinline__ static uint32_t half_mask(uint32_t bits) {
+        return prmt(bits << (15 - PP), 0, 0xbb99);
+    }
+    // lane bits of the local slots [lo, hi] (empty if lo > hi)
+    __device__ __forceinline__ static uint32_t range_bits(int32_t lo, int32_t hi) {
+        lo = max(lo, 0);
+        hi = min(hi, C - 1);
+        if (lo > hi) return 0u;
+        const uint32_t b = ((2u << hi) - 1u) & ~((1u << lo) - 1u);
+        return (b & ((1u << P) - 1u)) | ((b >> P) << 16);
+    }
+    __device__ __forceinline__ static uint32_t slot_bit(int32_t jl) {
+        if (jl < 0 || jl >= C) return 0u;
+        return jl < P ? (1u << jl) : (1u << (16 + jl - P));
     }
 
     // ------------------------------------------------------- Eq. 4-7 test
@@ -160,156 +176,77 @@ struct WarpPair16 {
         return false;
     }
 
-    template <int JL>
-    __device__ __forceinline__ static int32_t half(const uint32_t (&a)[P]) {
-        if constexpr (JL < P) return (int32_t)(a[JL] & 0xffffu);
-        else return (int32_t)(a[JL - P] >> 16);
-    }
-
-    // --------------------------------------------------------- masked step
-    // One cell in int32 arithmetic on u values, every edge case handled.
-    // d = 1 on odd anti-diagonals (E from j-1, F from j), 0 on even ones.
-    template <int JL>
-    __device__ __forceinline__ void masked_cell(int32_t r, int32_t B, int32_t d, uint32_t nm,
-                                                int32_t eL, int32_t e2L, int32_t fR, int32_t f2R,
-                                                int32_t &oH, int32_t &oE, int32_t &oE2,
-                                                int32_t &oF, int32_t &oF2, int32_t &best,
-                                                int32_t &best_j, int32_t &te_c, int32_t &qe_c) {
-        const int32_t t = B + j0 + JL, q = r - t;
-        int32_t Ein, E2in, Fin, F2in;
-        if constexpr (JL == 0) {
-            Ein = d ? eL : half<0>(Eo);
-            E2in = d ? e2L : half<0>(E2o);
-        } else {
-            Ein = d ? half<JL - 1>(Eo) : half<JL>(Eo);
-            E2in = d ? half<JL - 1>(E2o) : half<JL>(E2o);
-        }
-        if constexpr (JL == C - 1) {
-            Fin = d ? half<JL>(Fo) : fR;
-            F2in = d ? half<JL>(F2o) : f2R;
-        } else {
-            Fin = d ? half<JL>(Fo) : half<JL + 1>(Fo);
-            F2in = d ? half<JL>(F2o) : half<JL + 1>(F2o);
-        }
-        const int32_t s = ((nm >> (2 * JL)) & 1u) ? -prm.b : prm.a;
-        int32_t H = max(max(half<JL>(H2) + s, Ein), max(max(Fin, E2in), F2in));
-        int32_t ne = max(H - oe, Ein - prm.e), nf = max(H - oe, Fin - prm.e);
-        int32_t ne2 = max(H - oe2, E2in - prm.e2), nf2 = max(H - oe2, F2in - prm.e2);
-        const int32_t k = t - q;
-        const bool real = t >= 0 && q >= 0 && t < tlen && q < qlen && k <= w && -k <= w;
-        if (real) {
-            if (H < (int32_t)U_NEG + 2 * Dp || H > 0xffff - Dp) ovf = true;
-            if (H > best) { best = H; best_j = JL; }
-            if (t == tlen - 1) te_c = H;
-            if (q == qlen - 1) qe_c = H;
-        } else {
-            const bool virt = (t == -1 && q >= -1 && q < qlen) || (q == -1 && t >= 0 && t < tlen);
-            if (virt) {
-                const int32_t v = (t == -1 && q == -1) ? 0 : -gap_cost(prm, (t == -1 ? q : t) + 1);
-                H = to_u(v);
-                if (H < (int32_t)U_NEG + 2 * Dp || H > 0xffff - Dp) ovf = true;
-                ne = nf = H - oe;
-                ne2 = nf2 = H - oe2;
-            } else {
-                H = ne = nf = ne2 = nf2 = (int32_t)U_NEG;
-            }
-        }
-        oH = H; oE = ne; oE2 = ne2; oF = nf; oF2 = nf2;
-    }
-
-    template <int PP>
-    __device__ __forceinline__ void masked_pair(int32_t r, int32_t B, int32_t d, uint32_t nm,
-                                                int32_t eL, int32_t e2L, int32_t fR, int32_t f2R,
-                                                uint32_t (&nH)[P], uint32_t (&nE)[P],
-                                                uint32_t (&nE2)[P], uint32_t (&nF)[P],
-                                                uint32_t (&nF2)[P], int32_t &lo_best,
-                                                int32_t &lo_j, int32_t &hi_best, int32_t &hi_j,
-                                                int32_t &te_c, int32_t &qe_c) {
-        int32_t h0, e0, e20, f0, f20, h1, e1, e21, f1, f21;
-        masked_cell<PP>(r, B, d, nm, eL, e2L, fR, f2R, h0, e0, e20, f0, f20, lo_best, lo_j, te_c, qe_c);
-        masked_cell<PP + P>(r, B, d, nm, eL, e2L, fR, f2R, h1, e1, e21, f1, f21, hi_best, hi_j, te_c,
-                            qe_c);
-        nH[PP] = (uint32_t)(h0 & 0xffff) | ((uint32_t)(h1 & 0xffff) << 16);
-        nE[PP] = (uint32_t)(e0 & 0xffff) | ((uint32_t)(e1 & 0xffff) << 16);
-        nE2[PP] = (uint32_t)(e20 & 0xffff) | ((uint32_t)(e21 & 0xffff) << 16);
-        nF[PP] = (uint32_t)(f0 & 0xffff) | ((uint32_t)(f1 & 0xffff) << 16);
-        nF2[PP] = (uint32_t)(f20 & 0xffff) | ((uint32_t)(f21 & 0xffff) << 16);
-        if constexpr (PP + 1 < P)
-            masked_pair<PP + 1>(r, B, d, nm, eL, e2L, fR, f2R, nH, nE, nE2, nF, nF2, lo_best, lo_j,
-                                hi_best, hi_j, te_c, qe_c);
-    }
-
-    __device__ __forceinline__ bool masked_step(int32_t r) {
-        const int32_t B = frame(r);
-        const int32_t d = (r - w) & 1;
-        if (r >= 0) {
-            const int32_t st = max(max(0, r - qlen + 1), ceil_div2(r - w));
-            const int32_t en = min(min(tlen - 1, r), floor_div2(r + w));
-            if (st > en) { zdropped = 1; return true; }      // the band left the table
-            cells += en - st + 1;
-        }
-        const uint32_t eLp = __shfl_up_sync(FULL, Eo[P - 1], 1);
-        const uint32_t e2Lp = __shfl_up_sync(FULL, E2o[P - 1], 1);
-        const uint32_t fRp = __shfl_down_sync(FULL, Fo[0], 1);
-        const uint32_t f2Rp = __shfl_down_sync(FULL, F2o[0], 1);
-        int32_t eL = (int32_t)(eLp >> 16), e2L = (int32_t)(e2Lp >> 16);
-        int32_t fR = (int32_t)(fRp & 0xffffu), f2R = (int32_t)(f2Rp & 0xffffu);
-        // slot 0 of lane 0 takes E from slot -1 only on odd anti-diagonals,
-        // where it is outside the band or a virtual cell: its input never counts
-        if (lane == 0) eL = e2L = (int32_t)U_NEG;
-        if (lane == 31) {
-            // F of the last slot on even anti-diagonals: slot 32C of r-1, the
-            // virtual column cell (t, -1) when q == -1 there, else outside
-            const int32_t ts = frame(r - 1) + 32 * C, qs = r - 1 - ts;
-            if (qs == -1 && ts >= 0 && ts < tlen) {
-                const int32_t v = to_u(-gap_cost(prm, ts + 1));
-                if (v < (int32_t)U_NEG + 2 * Dp || v > 0xffff - Dp) ovf = true;
-                fR = v - oe; f2R = v - oe2;
-            } else {
-                fR = f2R = (int32_t)U_NEG;
-            }
-        }
-        const uint32_t nm = mismatch_bits();
-        uint32_t nH[P], nE[P], nE2[P], nF[P], nF2[P];
-        int32_t lo_best = INT_MIN, lo_j = -1, hi_best = INT_MIN, hi_j = -1;
-        int32_t te_c = INT_MIN, qe_c = INT_MIN;
-        masked_pair<0>(r, B, d, nm, eL, e2L, fR, f2R, nH, nE, nE2, nF, nF2, lo_best, lo_j, hi_best,
-                       hi_j, te_c, qe_c);
-#pragma unroll
-        for (int p = 0; p < P; ++p) {
-            H2[p] = H1[p]; H1[p] = nH[p];
-            Eo[p] = nE[p]; E2o[p] = nE2[p]; Fo[p] = nF[p]; F2o[p] = nF2[p];
-        }
-        if (__any_sync(FULL, ovf)) { ovf = true; return true; }
-        if (r < 0) return false;
-        const int32_t te_v = __reduce_max_sync(FULL, te_c);
-        if (te_v != INT_MIN && to_true(te_v) > mte) { mte = to_true(te_v); mte_q = r - (tlen - 1); }
-        const int32_t qe_v = __reduce_max_sync(FULL, qe_c);
-        if (qe_v != INT_MIN && to_true(qe_v) > mqe) { mqe = to_true(qe_v); mqe_t = r - (qlen - 1); }
-        // lowest-index maximum of the lane: low halves hold the smaller slots
-        const int32_t lm = lo_best >= hi_best ? lo_best : hi_best;
-        const int32_t li = lo_best >= hi_best ? lo_j : hi_j;
+    // Anti-diagonal maximum and termination rule.  lmax: 16x2 maximum of
+    // H - q - e over the lane's band cells (others 0); Hn: the H values of r;
+    // excl(p): 0xFFFF halves of slots that are not band cells.  Returns true
+    // to stop.
+    template <bool ODD, typename Excl>
+    __device__ __forceinline__ bool anti_diagonal_max(int32_t r, int32_t B, uint32_t lmax,
+                                                      const uint32_t (&Hn)[P], Excl excl) {
+        const int32_t lm = (int32_t)max(lmax & 0xffffu, lmax >> 16);
         const int32_t m = __reduce_max_sync(FULL, lm);
-        const unsigned ball = __ballot_sync(FULL, lm == m && li >= 0);
-        const int src = __ffs(ball) - 1;
-        const int32_t lj = __shfl_sync(FULL, li, src);
-        if (max_and_zdrop(to_true(m), B + src * C + lj, r)) { zdropped = 1; return true; }
-        if (r == last_r && te_v != INT_MIN && (r - (tlen - 1)) == qlen - 1) gscore = to_true(te_v);
-        if (++since >= U_K - 2) rebase(m, r);
-        return ovf;
+        const int32_t mt = to_true(m + oe);
+        last_m = m + oe;
+        if (mt > gmax || (prm.zdrop >= 0 && gmax - mt > prm.zdrop)) {
+            // position only when it can matter: lowest slot of the first lane
+            // holding the maximum; bit p / 16+p of `ne` is set where the low /
+            // high half of register p is not it
+            const unsigned ball = __ballot_sync(FULL, lm == m);
+            const int src = __ffs(ball) - 1;
+            const uint32_t mh2 = (uint32_t)(m + oe) * 0x10001u;
+            uint32_t ne = 0;
+#pragma unroll
+            for (int p = 0; p < P; ++p) ne += __vminu2((Hn[p] ^ mh2) | excl(p), 0x10001u) << p;
+            const uint32_t eq = ~ne & ((((1u << P) - 1) << 16) | ((1u << P) - 1));
+            const uint32_t lo_eq = eq & 0xffffu, hi_eq = eq >> 16;
+            const int32_t jl = lo_eq ? __ffs(lo_eq) - 1 : P + __ffs(hi_eq) - 1;
+            const int32_t lj = __shfl_sync(FULL, jl, src);
+            if (max_and_zdrop(mt, B + src * C + lj, r)) { zdropped = 1; return true; }
+        }
+        return false;
     }
 
-    // ----------------------------------------------------------- bulk step
-    // One bulk anti-diagonal on the packed registers, in place: Hd holds H of
-    // r-2 on entry and H of r on exit, the gap arrays hold the states leaving
-    // r-1 on entry and r on exit.  ODD: (r - w) odd.  Applies the
-    // termination rule to the anti-diagonal; returns true to stop.
-    template <bool ODD>
-    __device__ __forceinline__ bool cell_step(int32_t r, uint32_t (&Hd)[P]) {
+    // One anti-diagonal on the packed registers, in place (H(r) replaces
+    // H(r-2) in the array of its parity, the gap arrays turn from the states
+    // leaving r-1 into those leaving r).  ODD: (r - w) odd, E from slot j-1
+    // and F from slot j; else E from slot j and F from slot j+1.  F-from-j+1
+    // steps walk the registers upwards and E-from-j-1 steps downwards, so
+    // every old value is read before it is overwritten.
+    //
+    // MASKED: the band meets the table's edges on r.  After the update every
+    // slot is set to what the recurrence defines there: a band cell keeps its
+    // value, the virtual row/column cell (-1, r+1) or (r+1, -1) gets
+    // H = -gap(r+2) (H(-1,-1) = 0 on r = -2), anything else is minus infinity.
+    template <bool ODD, bool MASKED>
+    __device__ __forceinline__ bool step(int32_t r) {
+        uint32_t (&Hd)[P] = ODD ? Hod : Hev;
         const int32_t B = frame(r);
+        int32_t st = 0, en = -1;
+        uint32_t rb = 0, vb = 0, tb = 0, qb = 0, VVp = 0, VVe = 0, VVe2 = 0;
+        bool te_real = false, qe_real = false;
+        if constexpr (MASKED) {
+            if (r >= 0) {
+                st = max(max(0, r - qlen + 1), ceil_div2(r - w));
+                en = min(min(tlen - 1, r), floor_div2(r + w));
+                if (st > en) { zdropped = 1; return true; }  // the band left the table
+            }
+            rb = range_bits(st - B - j0, en - B - j0);
+            if (r + 1 < qlen) vb |= slot_bit(-1 - B - j0);                 // (-1, r+1)
+            if (r >= -1 && r + 1 < tlen) vb |= slot_bit(r + 1 - B - j0);  // (r+1, -1)
+            const int32_t vv = to_u(r == -2 ? 0 : -gap_cost(prm, r + 2));
+            if (__any_sync(FULL, vb != 0u) && (vv < LOWCHK || vv > 0xffff - Dp)) ovf = true;
+            VVp = (uint32_t)vv * 0x10001u;
+            VVe = (uint32_t)(vv - oe) * 0x10001u;
+            VVe2 = (uint32_t)(vv - oe2) * 0x10001u;
+            te_real = r >= 0 && st <= tlen - 1 && tlen - 1 <= en;
+            qe_real = r >= 0 && st <= r - qlen + 1 && r - qlen + 1 <= en;
+            tb = te_real ? slot_bit(tlen - 1 - B - j0) : 0u;
+            qb = qe_real ? slot_bit(r - qlen + 1 - B - j0) : 0u;
+        }
         uint32_t edge, edge2;
         if constexpr (ODD) {
-            // E of slot 0 from the left lane's last slot (high half of its last register)
+            // E of slot 0 from the left lane's last slot (high half of its last
+            // register); for lane 0 it would feed slot 0, outside the band here
             const uint32_t eL = __shfl_up_sync(FULL, Eo[P - 1], 1);
             const uint32_t e2L = __shfl_up_sync(FULL, E2o[P - 1], 1);
             edge = mux(L0LO, NEGp, prmt(eL, Eo[P - 1], 0x5432));
@@ -318,14 +255,26 @@ struct WarpPair16 {
             // F of the last slot from the right lane's first slot (low half of its register 0)
             const uint32_t fR = __shfl_down_sync(FULL, Fo[0], 1);
             const uint32_t f2R = __shfl_down_sync(FULL, F2o[0], 1);
-            edge = mux(L31HI, NEGp, prmt(Fo[0], fR, 0x5432));
-            edge2 = mux(L31HI, NEGp, prmt(F2o[0], f2R, 0x5432));
+            uint32_t inj = NEGp, inj2 = NEGp;
+            if (MASKED && lane == 31) {
+                // beyond the last lane: slot 32C of r-1, the virtual column
+                // cell (t, -1) when q == -1 there
+                const int32_t ts = frame(r - 1) + 32 * C, qs = r - 1 - ts;
+                if (qs == -1 && ts >= 0 && ts < tlen) {
+                    const int32_t v = to_u(-gap_cost(prm, ts + 1));
+                    if (v < LOWCHK || v > 0xffff - Dp) ovf = true;
+                    inj = ((uint32_t)(v - oe) << 16) | (NEGp & 0xffffu);
+                    inj2 = ((uint32_t)(v - oe2) << 16) | (NEGp & 0xffffu);
+                }
+            }
+            edge = mux(L31HI, inj, prmt(Fo[0], fR, 0x5432));
+            edge2 = mux(L31HI, inj2, prmt(F2o[0], f2R, 0x5432));
         }
         const uint32_t comb = packed_mismatch();
-        uint32_t lmax = 0;
+        uint32_t lmax = 0, tmax = 0, qmax = 0;
 #pragma unroll
         for (int i = 0; i < P; ++i) {
-            const int p = ODD ? P - 1 - i : i;       // read every old value before overwriting it
+            const int p = ODD ? P - 1 - i : i;
             uint32_t Ein, E2in, Fin, F2in;
             if constexpr (ODD) {
                 Ein = p ? Eo[p - 1] : edge;
@@ -344,53 +293,71 @@ struct WarpPair16 {
             uint32_t H = __viaddmax_u16x2(Hd[p], s2, Ein);
             H = __vmaxu2(H, Fin);
             H = __vmaxu2(H, __vmaxu2(E2in, F2in));
-            const uint32_t dead = (ODD && p == 0) ? DM0odd : DM[p];
-            const uint32_t hoe = mux(dead, NEGp, H - OEp);
-            const uint32_t hoe2 = hoe - DOEp;
-            Eo[p] = __vmaxu2(Ein - Ep, hoe);
-            Fo[p] = __vmaxu2(Fin - Ep, hoe);
-            E2o[p] = __vmaxu2(E2in - E2p, hoe2);
-            F2o[p] = __vmaxu2(F2in - E2p, hoe2);
-            Hd[p] = H;
-            lmax = __vmaxu2(lmax, hoe);
-        }
-        // anti-diagonal maximum (of H - q - e, in u); its position is only
-        // needed when it is a new global maximum or a possible Z-drop
-        const int32_t lm = (int32_t)max(lmax & 0xffffu, lmax >> 16);
-        const int32_t m = __reduce_max_sync(FULL, lm);
-        const int32_t mt = to_true(m + oe);
-        cells += w + 1 - (ODD ? 1 : 0);
-        if (mt > gmax || (prm.zdrop >= 0 && gmax - mt > prm.zdrop)) {
-            // lowest slot of the first lane holding the maximum: bit p / 16+p
-            // of `ne` is set where the low / high half of register p is not it
-            const unsigned ball = __ballot_sync(FULL, lm == m);
-            const int src = __ffs(ball) - 1;
-            const uint32_t mh2 = (uint32_t)(m + oe) * 0x10001u;
-            uint32_t ne = 0;
-#pragma unroll
-            for (int p = 0; p < P; ++p) {
+            if constexpr (!MASKED) {
                 const uint32_t dead = (ODD && p == 0) ? DM0odd : DM[p];
-                ne += __vminu2((Hd[p] ^ mh2) | dead, 0x10001u) << p;
+                const uint32_t hoe = mux(dead, NEGp, H - OEp);
+                const uint32_t hoe2 = hoe - DOEp;
+                Eo[p] = __vmaxu2(Ein - Ep, hoe);
+                Fo[p] = __vmaxu2(Fin - Ep, hoe);
+                E2o[p] = __vmaxu2(E2in - E2p, hoe2);
+                F2o[p] = __vmaxu2(F2in - E2p, hoe2);
+                Hd[p] = H;
+                lmax = __vmaxu2(lmax, hoe);
+            } else {
+                const uint32_t hoe = H - OEp;
+                const uint32_t hoe2 = hoe - DOEp;
+                const uint32_t rm = prmt(rb << (15 - p), 0, 0xbb99);
+                const uint32_t vm = prmt(vb << (15 - p), 0, 0xbb99);
+                const uint32_t fillE = mux(vm, VVe, NEGp);
+                const uint32_t fillE2 = mux(vm, VVe2, NEGp);
+                Eo[p] = mux(rm, __vmaxu2(Ein - Ep, hoe), fillE);
+                Fo[p] = mux(rm, __vmaxu2(Fin - Ep, hoe), fillE);
+                E2o[p] = mux(rm, __vmaxu2(E2in - E2p, hoe2), fillE2);
+                F2o[p] = mux(rm, __vmaxu2(F2in - E2p, hoe2), fillE2);
+                Hd[p] = mux(rm, H, mux(vm, VVp, NEGp));
+                lmax = __vmaxu2(lmax, rm & hoe);
+                tmax = __vmaxu2(tmax, prmt(tb << (15 - p), 0, 0xbb99) & H);
+                qmax = __vmaxu2(qmax, prmt(qb << (15 - p), 0, 0xbb99) & H);
             }
-            const uint32_t eq = ~ne & ((((1u << P) - 1) << 16) | ((1u << P) - 1));
-            const uint32_t lo_eq = eq & 0xffffu, hi_eq = eq >> 16;
-            const int32_t jl = lo_eq ? __ffs(lo_eq) - 1 : P + __ffs(hi_eq) - 1;
-            const int32_t lj = __shfl_sync(FULL, jl, src);
-            if (max_and_zdrop(mt, B + src * C + lj, r)) { zdropped = 1; return true; }
         }
-        last_m = m + oe;
-        return false;
+        if constexpr (!MASKED) {
+            cells += w + 1 - (ODD ? 1 : 0);
+            return anti_diagonal_max<ODD>(r, B, lmax, Hd, [&](int p) {
+                return (ODD && p == 0) ? DM0odd : DM[p];
+            });
+        } else {
+            if (__any_sync(FULL, ovf)) { ovf = true; return true; }
+            if (r < 0) return false;
+            cells += en - st + 1;
+            // best score on the last target row / the last query column
+            if (te_real) {
+                const int32_t tv = __reduce_max_sync(FULL, (int32_t)max(tmax & 0xffffu, tmax >> 16));
+                if (to_true(tv) > mte) { mte = to_true(tv); mte_q = r - (tlen - 1); }
+                if (r == last_r) gscore = to_true(tv);     // set below unless Z-drop stops r
+            }
+            if (qe_real) {
+                const int32_t qv = __reduce_max_sync(FULL, (int32_t)max(qmax & 0xffffu, qmax >> 16));
+                if (to_true(qv) > mqe) { mqe = to_true(qv); mqe_t = r - (qlen - 1); }
+            }
+            const int32_t gs = gscore;
+            if (r == last_r) gscore = K_NEG_OUT;
+            if (anti_diagonal_max<ODD>(r, B, lmax, Hd, [&](int p) {
+                    return ~prmt(rb << (15 - p), 0, 0xbb99);
+                }))
+                return true;
+            if (r == last_r) gscore = gs;
+            if (++since >= U_K - 2) rebase(last_m, r);
+            return ovf;
+        }
     }
 
-    // Bulk anti-diagonals r ((r - w) even) and r+1.  On entry H2 = H(r-2),
-    // H1 = H(r-1), gap states leave r-1; on exit the same for r+1 (H2 ends up
-    // holding H(r) and H1 H(r+1), the canonical order).  Returns 0 to go on,
-    // else k+1 when the extension stopped on r+k.
+    // Bulk anti-diagonals r ((r - w) even) and r+1; returns 0 to go on, else
+    // k+1 when the extension stopped on r+k.
     __device__ __forceinline__ int fast_pair(int32_t r) {
         shift_t();
-        if (cell_step<false>(r, H2)) return 1;
+        if (step<false, false>(r)) return 1;
         shift_q();
-        if (cell_step<true>(r + 1, H1)) return 2;
+        if (step<true, false>(r + 1)) return 2;
         since += 2;
         if (since >= U_K - 2) {
             rebase(last_m, r + 1);
@@ -398,7 +365,10 @@ struct WarpPair16 {
         }
         return 0;
     }
-    int32_t last_m;
+
+    __device__ __forceinline__ bool masked_step(int32_t r) {
+        return ((r - w) & 1) ? step<true, true>(r) : step<false, true>(r);
+    }
 
     // ---------------------------------------------------------------- rebase
     // Move base so that the anti-diagonal maximum m_u is stored at OFF; check
@@ -413,7 +383,7 @@ struct WarpPair16 {
         else { if (hi < low) ovf = true; hi = min(max(hi - delta, (int32_t)U_NEG + 1), 0xffff); }
         x = (uint32_t)lo | ((uint32_t)hi << 16);
     }
-    // H1 = H(r), H2 = H(r-1), gap states leave r
+    // r: the last anti-diagonal computed (its gap states are in Eo..)
     __device__ __forceinline__ void rebase(int32_t m_u, int32_t r) {
         since = 0;
         const int32_t delta = m_u - OFF;
@@ -423,9 +393,8 @@ struct WarpPair16 {
         for (int p = 0; p < P; ++p) {
             const uint32_t dm_odd = p == 0 ? DM0odd : DM[p];
             const uint32_t dm_r = odd ? dm_odd : DM[p];       // slots of anti-diagonal r
-            const uint32_t dm_r1 = odd ? DM[p] : dm_odd;      // slots of r-1
-            rebase_reg(H1[p], dm_r, delta, low);
-            rebase_reg(H2[p], dm_r1, delta, low);
+            rebase_reg(Hev[p], DM[p], delta, low);
+            rebase_reg(Hod[p], dm_odd, delta, low);
             rebase_reg(Eo[p], dm_r, delta, low);
             rebase_reg(E2o[p], dm_r, delta, low);
             rebase_reg(Fo[p], dm_r, delta, low);
@@ -457,6 +426,7 @@ struct WarpPair16 {
         OFF = 0xffff - (U_K + 3) * Dp;
         base = 0;
         since = 0;
+        last_m = OFF;
         ovf = false;
         A2 = ((uint32_t)prm.a & 0xffffu) * 0x10001u;
         NB2 = ((uint32_t)(-prm.b) & 0xffffu) * 0x10001u;
@@ -471,7 +441,7 @@ struct WarpPair16 {
         for (int p = 0; p < P; ++p) {
             const int32_t jlo = j0 + p, jhi = j0 + p + P;
             DM[p] = (jlo > w ? 0x0000ffffu : 0u) | (jhi > w ? 0xffff0000u : 0u);
-            H1[p] = H2[p] = Eo[p] = E2o[p] = Fo[p] = F2o[p] = NEGp;
+            Hev[p] = Hod[p] = Eo[p] = E2o[p] = Fo[p] = F2o[p] = NEGp;
         }
         DM0odd = DM[0] | L0LO;
         gmax = 0; gt = -1; gq = -1;
@@ -487,8 +457,8 @@ struct WarpPair16 {
             advance(r);
             stop = masked_step(r);
         }
-        // bulk: pairs starting at r = w + 2 ((r - w) even) while every band cell
-        // of the pair is a real cell away from the last row and column
+        // bulk: pairs starting at r = w + 2 ((r - w) even) while every band
+        // cell of the pair is a real cell away from the last row and column
         const int32_t L = min(tlen, qlen);
         const int32_t bulk_last = 2 * L - 3 - w;
         if (use_fast && !stop && r == w + 1) {
