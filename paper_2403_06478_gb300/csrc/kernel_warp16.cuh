@@ -94,7 +94,7 @@ struct WarpPair16 {
     int32_t base, Dp, LOWCHK, OFF, since, last_m;
     bool ovf;
     // packed constants
-    uint32_t A2, NB2, OEp, DOEp, Ep, E2p, NEGp, L0LO, L31HI;
+    uint32_t A2, NB2, OEp, DOEp, Ep, E2p, NEp, NE2p, NEGp, L0LO, L31HI;
     // bookkeeping (uniform across the warp)
     int32_t gmax, gt, gq, mqe, mqe_t, mte, mte_q, gscore;
     int64_t cells;
@@ -297,10 +297,11 @@ struct WarpPair16 {
                 const uint32_t dead = (ODD && p == 0) ? DM0odd : DM[p];
                 const uint32_t hoe = mux(dead, NEGp, H - OEp);
                 const uint32_t hoe2 = hoe - DOEp;
-                Eo[p] = __vmaxu2(Ein - Ep, hoe);
-                Fo[p] = __vmaxu2(Fin - Ep, hoe);
-                E2o[p] = __vmaxu2(E2in - E2p, hoe2);
-                F2o[p] = __vmaxu2(F2in - E2p, hoe2);
+                // per-half add of -e (wraps within the half) then max: one op each
+                Eo[p] = __viaddmax_u16x2(Ein, NEp, hoe);
+                Fo[p] = __viaddmax_u16x2(Fin, NEp, hoe);
+                E2o[p] = __viaddmax_u16x2(E2in, NE2p, hoe2);
+                F2o[p] = __viaddmax_u16x2(F2in, NE2p, hoe2);
                 Hd[p] = H;
                 lmax = __vmaxu2(lmax, hoe);
             } else {
@@ -434,6 +435,8 @@ struct WarpPair16 {
         DOEp = (uint32_t)(oe2 - oe) * 0x10001u;
         Ep = (uint32_t)prm.e * 0x10001u;
         E2p = (uint32_t)prm.e2 * 0x10001u;
+        NEp = ((uint32_t)(-prm.e) & 0xffffu) * 0x10001u;
+        NE2p = ((uint32_t)(-prm.e2) & 0xffffu) * 0x10001u;
         NEGp = U_NEG * 0x10001u;
         L0LO = lane == 0 ? 0x0000ffffu : 0u;
         L31HI = lane == 31 ? 0xffff0000u : 0u;
