@@ -290,9 +290,9 @@ struct WarpPair16 {
             // substitution: mismatch bits of both halves replicated to 0xFFFF masks
             const uint32_t mm = prmt(comb << (15 - 2 * p), 0, 0xbb99);
             const uint32_t s2 = mux(mm, NB2, A2);
-            uint32_t H = __viaddmax_u16x2(Hd[p], s2, Ein);
-            H = __vmaxu2(H, Fin);
-            H = __vmaxu2(H, __vmaxu2(E2in, F2in));
+            // H = max(H(r-2) + s, E, F, E2, F2): add-max, 3-input max, max
+            const uint32_t H = __vmaxu2(__vimax3_u16x2(__viaddmax_u16x2(Hd[p], s2, Ein), Fin, E2in),
+                                        F2in);
             if constexpr (!MASKED) {
                 const uint32_t dead = (ODD && p == 0) ? DM0odd : DM[p];
                 const uint32_t hoe = mux(dead, NEGp, H - OEp);
@@ -311,10 +311,10 @@ struct WarpPair16 {
                 const uint32_t vm = prmt(vb << (15 - p), 0, 0xbb99);
                 const uint32_t fillE = mux(vm, VVe, NEGp);
                 const uint32_t fillE2 = mux(vm, VVe2, NEGp);
-                Eo[p] = mux(rm, __vmaxu2(Ein - Ep, hoe), fillE);
-                Fo[p] = mux(rm, __vmaxu2(Fin - Ep, hoe), fillE);
-                E2o[p] = mux(rm, __vmaxu2(E2in - E2p, hoe2), fillE2);
-                F2o[p] = mux(rm, __vmaxu2(F2in - E2p, hoe2), fillE2);
+                Eo[p] = mux(rm, __viaddmax_u16x2(Ein, NEp, hoe), fillE);
+                Fo[p] = mux(rm, __viaddmax_u16x2(Fin, NEp, hoe), fillE);
+                E2o[p] = mux(rm, __viaddmax_u16x2(E2in, NE2p, hoe2), fillE2);
+                F2o[p] = mux(rm, __viaddmax_u16x2(F2in, NE2p, hoe2), fillE2);
                 Hd[p] = mux(rm, H, mux(vm, VVp, NEGp));
                 lmax = __vmaxu2(lmax, rm & hoe);
                 tmax = __vmaxu2(tmax, prmt(tb << (15 - p), 0, 0xbb99) & H);
