@@ -497,7 +497,7 @@ struct WarpPair16 {
 };
 
 template <int C>
-__global__ void __launch_bounds__(WARP_BLOCK_THREADS, 3)
+__global__ void __launch_bounds__(WARP_BLOCK_THREADS, 4)
 warp16_align_kernel(const DevBatch *__restrict__ d_batch, int32_t use_fast) {
     const DevBatch B = *d_batch;
     const int lane = threadIdx.x & 31;
