@@ -181,12 +181,24 @@ int64_t agatha_band_cells(int32_t tlen, int32_t qlen, int32_t w);
 
 /* ---------------------------------------------------------------------- */
 /* Serving: continuous batching of alignment requests on one device.       */
+/* Not an operation of the paper, which aligns one prepared batch; it feeds */
+/* the batched kernels (Section 4) from a stream of small requests.         */
+/*                                                                          */
+/* A scheduler thread merges queued requests that share their (normalised)  */
+/* scoring into one batch of at most max_batch_pairs pairs whenever one of  */
+/* max_inflight launch slots is free, and runs it like agatha_align_batch.  */
+/* Every launch holds one block of a device arena of mem_budget_bytes made  */
+/* at start; a request too large for the whole arena is refused, a batch   */
+/* that does not fit now waits, so requests never hold more device memory   */
+/* than the budget (plus about 4 KiB of fixed scratch per slot).  Results   */
+/* are those agatha_align_batch gives each request on its own.              */
 
 typedef struct {
-    int64_t mem_budget_bytes;   /* device bytes admitted requests may hold */
-    int32_t max_inflight;       /* requests on the device at once (>= 1)   */
-    int32_t max_batch_pairs;    /* pairs merged into one device launch     */
-    int32_t linger_us;          /* wait this long for more requests        */
+    int64_t mem_budget_bytes;   /* arena for admitted requests; 0: 1 GiB   */
+    int32_t max_inflight;       /* launch slots on the device; 0: 2, <= 16 */
+    int32_t max_batch_pairs;    /* pairs merged into one launch; 0: 8192   */
+    int32_t linger_us;          /* hold a short head batch this long for   */
+                                /* more requests; 0: launch at once        */
     int32_t pad;
 } agatha_serve_config;
 
@@ -199,12 +211,14 @@ typedef struct {
 } agatha_serve_stats;
 
 /* Start the scheduler thread of ctx (one server per context).  EINVAL on a
- * bad config, EAGAIN if already serving. */
+ * bad config, EAGAIN if already serving, ENOMEM if the arena cannot be
+ * allocated.  Independent of agatha_align_batch on the same context. */
 int agatha_serve_start(agatha_ctx *ctx, const agatha_serve_config *cfg);
 
 /* Submit a request (host pointers; copied before return).  `out` (host,
  * n_pairs results) must stay valid until the ticket completes.  ENOMEM if the
- * request alone exceeds the memory budget; EINVAL on a bad batch. */
+ * request alone exceeds the memory budget; EINVAL on a bad batch or when the
+ * server is not running; ENOTSUP for a band wider than supported. */
 int agatha_serve_submit(agatha_ctx *ctx, const agatha_batch *batch,
                         const agatha_params *params, agatha_result *out,
                         uint64_t *ticket);
@@ -213,15 +227,18 @@ int agatha_serve_submit(agatha_ctx *ctx, const agatha_batch *batch,
  * pending, AGATHA_ECANCELED if cancelled, EINVAL for an unknown ticket. */
 int agatha_serve_poll(agatha_ctx *ctx, uint64_t ticket);
 
-/* Wait up to timeout_ms (< 0: forever).  OK, ETIMEDOUT, ECANCELED, EINVAL.
- * A completed ticket is forgotten after a successful wait. */
+/* Wait up to timeout_ms (< 0: forever).  Returns the ticket's final status
+ * (OK, ECANCELED, EDEVICE, ECUDA), ETIMEDOUT, or EINVAL for an unknown
+ * ticket.  A ticket is forgotten once a wait returned its final status. */
 int agatha_serve_wait(agatha_ctx *ctx, uint64_t ticket, int32_t timeout_ms);
 
 /* Snapshot of the server's counters. */
 int agatha_serve_stats_get(agatha_ctx *ctx, agatha_serve_stats *stats);
 
 /* Stop the scheduler.  drain != 0: finish every admitted and queued request;
- * drain == 0: finish requests already on the device, cancel queued ones. */
+ * drain == 0: finish requests already on the device, cancel queued ones.
+ * Returns after the device work ended and the arena was freed; tickets stay
+ * readable until agatha_destroy or the next agatha_serve_start. */
 int agatha_serve_stop(agatha_ctx *ctx, int32_t drain);
 
 /* ---------------------------------------------------------------------- */

@@ -323,6 +323,67 @@ def agatha_align_batch_noalloc(q_packed, t_packed, q_off, t_off, q_len, t_len, o
            what="agatha_align_batch_noalloc")
 
 
+class Server:
+    """The serving loop of a context: ``agatha_serve_start`` ... ``agatha_serve_stop``.
+
+    ``submit`` copies the request's inputs before it returns; the result array
+    it hands back is filled by the library when the ticket completes and must
+    not be read before ``wait`` (or ``poll``) reports completion."""
+
+    def __init__(self, ctx: Context, mem_budget_bytes: int = 0, max_inflight: int = 0,
+                 max_batch_pairs: int = 0, linger_us: int = 0):
+        self.ctx = ctx
+        cfg = agatha_serve_config(int(mem_budget_bytes), int(max_inflight), int(max_batch_pairs),
+                                  int(linger_us), 0)
+        _check(lib().agatha_serve_start(ctx.handle, ctypes.byref(cfg)), ctx.handle,
+               "agatha_serve_start")
+        self._out = {}          # ticket -> result array the library writes into
+
+    def submit(self, pb: PackedBatch, scoring) -> int:
+        n = pb.n_pairs
+        out = np.zeros(max(n, 1), dtype=RESULT_DTYPE)
+        b = _host_batch(pb)
+        p = make_params(scoring)
+        t = ctypes.c_uint64()
+        _check(lib().agatha_serve_submit(self.ctx.handle, ctypes.byref(b), ctypes.byref(p),
+                                         out.ctypes.data, ctypes.byref(t)),
+               self.ctx.handle, "agatha_serve_submit")
+        self._out[int(t.value)] = out[:n]
+        return int(t.value)
+
+    def poll(self, ticket: int) -> int:
+        """AGATHA_OK, AGATHA_EAGAIN, AGATHA_ECANCELED ... (the raw code)."""
+        return int(lib().agatha_serve_poll(self.ctx.handle, ctypes.c_uint64(ticket)))
+
+    def wait_code(self, ticket: int, timeout_ms: int = -1) -> int:
+        """agatha_serve_wait's raw code; the ticket's results stay reachable
+        through ``result`` after AGATHA_OK."""
+        return int(lib().agatha_serve_wait(self.ctx.handle, ctypes.c_uint64(ticket),
+                                           ctypes.c_int32(timeout_ms)))
+
+    def result(self, ticket: int) -> np.ndarray:
+        return self._out.pop(ticket)
+
+    def wait(self, ticket: int, timeout_ms: int = -1) -> np.ndarray:
+        """Wait for a ticket and return its results; raises AgathaError otherwise."""
+        rc = self.wait_code(ticket, timeout_ms)
+        if rc != AGATHA_OK:
+            if rc != AGATHA_ETIMEDOUT:
+                self._out.pop(ticket, None)
+            _check(rc, self.ctx.handle, "agatha_serve_wait")
+        return self._out.pop(ticket)
+
+    def stats(self) -> dict:
+        st = agatha_serve_stats()
+        _check(lib().agatha_serve_stats_get(self.ctx.handle, ctypes.byref(st)), self.ctx.handle,
+               "agatha_serve_stats_get")
+        return {name: getattr(st, name) for name, _ in agatha_serve_stats._fields_}
+
+    def stop(self, drain: bool = True) -> None:
+        _check(lib().agatha_serve_stop(self.ctx.handle, ctypes.c_int32(1 if drain else 0)),
+               self.ctx.handle, "agatha_serve_stop")
+
+
 def agatha_init(device: int = 0, **kw) -> Context:
     return Context(device, **kw)
 

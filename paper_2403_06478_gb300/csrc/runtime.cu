@@ -56,25 +56,19 @@ int cuda_fail(agatha_ctx *ctx, cudaError_t e, const char *what) {
     return set_error(ctx, AGATHA_ECUDA, "%s: %s", what, cudaGetErrorString(e));
 }
 
-int DevBuf::ensure(agatha_ctx *ctx, size_t need) {
+// Grow a buffer to at least `need` bytes.  The caller has made sure no
+// device work still uses the old allocation.
+int DevBuf::ensure(agatha_ctx *ctx, Ledger &ledger, size_t need) {
     if (need <= cap) return AGATHA_OK;
     size_t want = std::max(need, cap + cap / 2);
     want = (want + 255) & ~(size_t)255;
-    const int64_t delta = (int64_t)want - (int64_t)cap;
-    if (ctx->mem_budget > 0 && ctx->mem_held + delta > ctx->mem_budget) {
+    need = (need + 255) & ~(size_t)255;
+    if (ledger.budget > 0 && ledger.held - (int64_t)cap + (int64_t)want > ledger.budget) {
         want = need;
-        if (ctx->mem_held + ((int64_t)want - (int64_t)cap) > ctx->mem_budget)
+        if (ledger.held - (int64_t)cap + (int64_t)want > ledger.budget)
             return set_error(ctx, AGATHA_ENOMEM, "device buffer of %zu bytes exceeds the budget", need);
     }
-    if (ptr) {
-        cudaStreamSynchronize(ctx->stream);
-        cudaFree(ptr);
-        ctx->mem_held -= (int64_t)cap;
-        ptr = nullptr;
-        cap = 0;
-    }
-    if (ctx->fail_alloc_after >= 0 && ctx->fail_alloc_after-- == 0)
-        return set_error(ctx, AGATHA_ENOMEM, "injected allocation failure");
+    release(ledger);
     cudaError_t e = cudaMalloc(&ptr, want);
     if (e != cudaSuccess) {
         ptr = nullptr;
@@ -82,13 +76,15 @@ int DevBuf::ensure(agatha_ctx *ctx, size_t need) {
         return set_error(ctx, AGATHA_ENOMEM, "cudaMalloc(%zu): %s", want, cudaGetErrorString(e));
     }
     cap = want;
-    ctx->mem_held += (int64_t)want;
-    ctx->graphs_stale = true;     // graphs may bake buffer addresses
+    ledger.held += (int64_t)want;
     return AGATHA_OK;
 }
 
-void DevBuf::release() {
-    if (ptr) cudaFree(ptr);
+void DevBuf::release(Ledger &ledger) {
+    if (ptr) {
+        cudaFree(ptr);
+        ledger.held -= (int64_t)cap;
+    }
     ptr = nullptr;
     cap = 0;
 }
@@ -192,45 +188,51 @@ int warp_occupancy(int C) {
     }
 }
 
-// Enqueue the device work of one batch whose descriptor is already on the
-// device, in two parts: part 0 = validation and ordering, part 1 = the
+// Enqueue the device work of one batch whose descriptor is already in the
+// slot, in two parts: part 0 = validation and ordering, part 1 = the
 // alignment kernels.  Each part is captured into its own CUDA graph (unless
-// the caller asked otherwise) so the timing events can sit between them.
-static cudaError_t enqueue_part(agatha_ctx *ctx, const LaunchPlan &lp, int part, cudaStream_t s) {
+// the caller asked otherwise) so timing events can sit between them.  The
+// kernels find every batch buffer through the descriptor, so a graph stays
+// valid when those buffers move; it bakes in only the slot's descriptor,
+// counters and histogram, which never move.
+static cudaError_t enqueue_part(agatha_ctx *ctx, Slot *sl, const LaunchPlan &lp, int part,
+                                cudaStream_t s) {
     cudaError_t e = cudaSuccess;
+    const DevBatch *d = sl->d_desc;
     if (part == 0) {
-        e = cudaMemsetAsync(ctx->counters.ptr, 0, CTR_COUNT * sizeof(int32_t), s);
+        e = cudaMemsetAsync(sl->counters.ptr, 0, CTR_COUNT * sizeof(int32_t), s);
         if (e != cudaSuccess) return e;
         if (!lp.plain) {
-            e = cudaMemsetAsync(ctx->hist.ptr, 0, 256 * sizeof(int64_t), s);
+            e = cudaMemsetAsync(sl->hist.ptr, 0, 256 * sizeof(int64_t), s);
             if (e != cudaSuccess) return e;
         }
         // the plain path only validates (no sort); the batched path also orders
-        return launch_prep(ctx->d_desc, lp.n, lp.plain ? 0 : lp.sort, s, ctx->n_sm);
+        return launch_prep(d, lp.n, lp.plain ? 0 : lp.sort, s, ctx->n_sm);
     }
-    if (lp.plain) return launch_plain_kernel(ctx->d_desc, lp.plain_blocks, lp.plain_w, 0, s);
+    if (lp.plain) return launch_plain_kernel(d, lp.plain_blocks, lp.plain_w, 0, s);
     if (lp.lane16) {
-        e = launch_warp16(lp.C16, ctx->d_desc, lp.warp16_blocks, s, lp.fast);
+        e = launch_warp16(lp.C16, d, lp.warp16_blocks, s, lp.fast);
         if (e != cudaSuccess) return e;
         // pairs whose scores left the 16-bit range, recomputed on int32 lanes
-        e = launch_warp(lp.C, ctx->d_desc, lp.warp_blocks, s, lp.fast, WARP_LIST_OVERFLOW);
+        e = launch_warp(lp.C, d, lp.warp_blocks, s, lp.fast, WARP_LIST_OVERFLOW);
     } else {
-        e = launch_warp(lp.C, ctx->d_desc, lp.warp_blocks, s, lp.fast, WARP_LIST_MAIN);
+        e = launch_warp(lp.C, d, lp.warp_blocks, s, lp.fast, WARP_LIST_MAIN);
     }
     if (e != cudaSuccess) return e;
-    if (lp.wide_w > 0) e = launch_plain_kernel(ctx->d_desc, (int64_t)ctx->n_sm * 2, lp.wide_w, 1, s);
+    if (lp.wide_w > 0) e = launch_plain_kernel(d, (int64_t)ctx->n_sm * 2, lp.wide_w, 1, s);
     return e;
 }
 
-static cudaError_t launch_part(agatha_ctx *ctx, const LaunchPlan &lp, int part, cudaStream_t s) {
-    if (!lp.use_graph) return enqueue_part(ctx, lp, part, s);
+static cudaError_t launch_part(agatha_ctx *ctx, Slot *sl, const LaunchPlan &lp, int part,
+                               cudaStream_t s) {
+    if (!lp.use_graph) return enqueue_part(ctx, sl, lp, part, s);
     const auto key = std::make_tuple(part, lp.key());
-    auto it = ctx->graphs.find(key);
-    if (it == ctx->graphs.end()) {
+    auto it = sl->graphs.find(key);
+    if (it == sl->graphs.end()) {
         cudaGraph_t g = nullptr;
         cudaError_t e = cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal);
         if (e != cudaSuccess) return e;
-        cudaError_t e1 = enqueue_part(ctx, lp, part, s);
+        cudaError_t e1 = enqueue_part(ctx, sl, lp, part, s);
         e = cudaStreamEndCapture(s, &g);
         if (e1 != cudaSuccess) { if (g) cudaGraphDestroy(g); return e1; }
         if (e != cudaSuccess) return e;
@@ -238,41 +240,73 @@ static cudaError_t launch_part(agatha_ctx *ctx, const LaunchPlan &lp, int part, 
         e = cudaGraphInstantiate(&ge, g, 0);
         cudaGraphDestroy(g);
         if (e != cudaSuccess) return e;
-        it = ctx->graphs.emplace(key, ge).first;
+        it = sl->graphs.emplace(key, ge).first;
     }
     return cudaGraphLaunch(it->second, s);
 }
 
-static cudaError_t run_plan(agatha_ctx *ctx, const LaunchPlan &lp, cudaStream_t s) {
-    if (ctx->graphs_stale) {
-        for (auto &kv : ctx->graphs) cudaGraphExecDestroy(kv.second);
-        ctx->graphs.clear();
-        ctx->graphs_stale = false;
-    }
-    cudaError_t e = launch_part(ctx, lp, 0, s);
+cudaError_t slot_run(agatha_ctx *ctx, Slot *sl, const LaunchPlan &lp, cudaStream_t s,
+                     cudaEvent_t ev0, cudaEvent_t ev1) {
+    cudaError_t e = launch_part(ctx, sl, lp, 0, s);
     if (e != cudaSuccess) return e;
-    if (ctx->timing && (e = cudaEventRecord(ctx->ev_k0, s)) != cudaSuccess) return e;
-    if ((e = launch_part(ctx, lp, 1, s)) != cudaSuccess) return e;
-    if (ctx->timing) e = cudaEventRecord(ctx->ev_k1, s);
+    if (ev0 && (e = cudaEventRecord(ev0, s)) != cudaSuccess) return e;
+    if ((e = launch_part(ctx, sl, lp, 1, s)) != cudaSuccess) return e;
+    if (ev1) e = cudaEventRecord(ev1, s);
     return e;
 }
 
-int ensure_batch_buffers(agatha_ctx *ctx, int64_t n, int64_t q_words, int64_t t_words,
-                         bool copy_inputs) {
+int slot_init(agatha_ctx *ctx, Ledger &ledger, Slot *sl) {
     int rc;
-    const int64_t n1 = std::max<int64_t>(n, 1);
-    if (copy_inputs) {
-        if ((rc = ctx->q_packed.ensure(ctx, (size_t)std::max<int64_t>(q_words, 1) * 4))) return rc;
-        if ((rc = ctx->t_packed.ensure(ctx, (size_t)std::max<int64_t>(t_words, 1) * 4))) return rc;
-        if ((rc = ctx->q_off.ensure(ctx, (size_t)n1 * 8))) return rc;
-        if ((rc = ctx->t_off.ensure(ctx, (size_t)n1 * 8))) return rc;
-        if ((rc = ctx->q_len.ensure(ctx, (size_t)n1 * 4))) return rc;
-        if ((rc = ctx->t_len.ensure(ctx, (size_t)n1 * 4))) return rc;
-        if ((rc = ctx->out.ensure(ctx, (size_t)n1 * sizeof(agatha_result)))) return rc;
+    if ((rc = sl->counters.ensure(ctx, ledger, CTR_COUNT * sizeof(int32_t))) ||
+        (rc = sl->hist.ensure(ctx, ledger, 256 * sizeof(int64_t))) ||
+        (rc = sl->desc.ensure(ctx, ledger, sizeof(DevBatch))))
+        return rc;
+    sl->d_desc = (DevBatch *)sl->desc.ptr;
+    if (cudaMallocHost(&sl->h_desc, sizeof(DevBatch)) != cudaSuccess ||
+        cudaMallocHost(&sl->h_counters, CTR_COUNT * sizeof(int32_t)) != cudaSuccess) {
+        cudaGetLastError();
+        return set_error(ctx, AGATHA_ENOMEM, "pinned host staging");
     }
-    if ((rc = ctx->order.ensure(ctx, (size_t)n1 * 4))) return rc;
-    if ((rc = ctx->wide_order.ensure(ctx, (size_t)n1 * 4))) return rc;
-    if ((rc = ctx->ovf_list.ensure(ctx, (size_t)n1 * 4))) return rc;
+    return AGATHA_OK;
+}
+
+void slot_release(Ledger &ledger, Slot *sl) {
+    for (auto &kv : sl->graphs) cudaGraphExecDestroy(kv.second);
+    sl->graphs.clear();
+    DevBuf *bufs[] = {&sl->q_packed, &sl->t_packed, &sl->q_off, &sl->t_off, &sl->q_len, &sl->t_len,
+                      &sl->out, &sl->order, &sl->wide_order, &sl->ovf_list, &sl->counters, &sl->hist,
+                      &sl->desc};
+    for (DevBuf *b : bufs) b->release(ledger);
+    if (sl->h_desc) cudaFreeHost(sl->h_desc);
+    if (sl->h_counters) cudaFreeHost(sl->h_counters);
+    sl->h_desc = nullptr;
+    sl->h_counters = nullptr;
+    sl->d_desc = nullptr;
+}
+
+int slot_ensure(agatha_ctx *ctx, Ledger &ledger, Slot *sl, int64_t n, int64_t q_words,
+                int64_t t_words, bool copy_inputs) {
+    const int64_t n1 = std::max<int64_t>(n, 1);
+    struct Need { DevBuf *b; size_t bytes; };
+    std::vector<Need> needs = {{&sl->order, (size_t)n1 * 4}, {&sl->wide_order, (size_t)n1 * 4},
+                               {&sl->ovf_list, (size_t)n1 * 4}};
+    if (copy_inputs) {
+        needs.push_back({&sl->q_packed, (size_t)std::max<int64_t>(q_words, 1) * 4});
+        needs.push_back({&sl->t_packed, (size_t)std::max<int64_t>(t_words, 1) * 4});
+        needs.push_back({&sl->q_off, (size_t)n1 * 8});
+        needs.push_back({&sl->t_off, (size_t)n1 * 8});
+        needs.push_back({&sl->q_len, (size_t)n1 * 4});
+        needs.push_back({&sl->t_len, (size_t)n1 * 4});
+        needs.push_back({&sl->out, (size_t)n1 * sizeof(agatha_result)});
+    }
+    bool grow = false;
+    for (const Need &x : needs) grow |= x.bytes > x.b->cap;
+    if (!grow) return AGATHA_OK;
+    // the previous batch of this slot may still read the buffers being replaced
+    if (sl->last_stream) cudaStreamSynchronize(sl->last_stream);
+    int rc;
+    for (const Need &x : needs)
+        if ((rc = x.b->ensure(ctx, ledger, x.bytes))) return rc;
     return AGATHA_OK;
 }
 
@@ -318,12 +352,13 @@ int make_plan(agatha_ctx *ctx, const DevParams &p, const BatchShape &shape, uint
     return AGATHA_OK;
 }
 
-void fill_desc(agatha_ctx *ctx, DevBatch *d, const DevParams &p, const LaunchPlan &lp) {
-    d->order = (lp.sort && !lp.plain) ? (int32_t *)ctx->order.ptr : nullptr;
-    d->counters = (int32_t *)ctx->counters.ptr;
-    d->wide_order = (int32_t *)ctx->wide_order.ptr;
-    d->bucket_hist = (int64_t *)ctx->hist.ptr;
-    d->ovf_list = (int32_t *)ctx->ovf_list.ptr;
+void fill_desc(const Slot *sl, DevBatch *d, const DevParams &p, const LaunchPlan &lp, void *order,
+               void *wide_order, void *ovf_list) {
+    d->order = (lp.sort && !lp.plain) ? (int32_t *)order : nullptr;
+    d->counters = (int32_t *)sl->counters.ptr;
+    d->wide_order = (int32_t *)wide_order;
+    d->bucket_hist = (int64_t *)sl->hist.ptr;
+    d->ovf_list = (int32_t *)ovf_list;
     d->params = p;
     d->warp_w_max = lp.plain ? INT32_MAX : lp.warp_w_max;
     d->pad = 0;
@@ -358,7 +393,7 @@ extern "C" int agatha_init(agatha_ctx **out, const agatha_config *cfg) {
     agatha_ctx *ctx = new (std::nothrow) agatha_ctx();
     if (!ctx) return AGATHA_ENOMEM;
     ctx->device = c.device;
-    ctx->mem_budget = c.mem_budget_bytes;
+    ctx->ledger.budget = c.mem_budget_bytes;
     if (c.tune_cache_path) ctx->tune_cache_path = c.tune_cache_path;
     if ((e = cudaSetDevice(c.device)) != cudaSuccess) { delete ctx; return AGATHA_ECUDA; }
     cudaDeviceProp prop;
@@ -370,19 +405,10 @@ extern "C" int agatha_init(agatha_ctx **out, const agatha_config *cfg) {
         delete ctx;
         return AGATHA_ECUDA;
     }
-    int rc;
-    if ((rc = ctx->counters.ensure(ctx, CTR_COUNT * sizeof(int32_t))) ||
-        (rc = ctx->hist.ensure(ctx, 256 * sizeof(int64_t))) ||
-        (rc = ctx->desc.ensure(ctx, sizeof(DevBatch)))) {
+    int rc = slot_init(ctx, ctx->ledger, &ctx->main);
+    if (rc) {
         agatha_destroy(ctx);
         return rc;
-    }
-    ctx->d_desc = (DevBatch *)ctx->desc.ptr;
-    if (cudaMallocHost(&ctx->h_desc, sizeof(DevBatch)) != cudaSuccess ||
-        cudaMallocHost(&ctx->h_counters, CTR_COUNT * sizeof(int32_t)) != cudaSuccess) {
-        cudaGetLastError();
-        agatha_destroy(ctx);
-        return AGATHA_ENOMEM;
     }
     if (c.flags & AGATHA_CFG_TIMING) {
         ctx->timing = true;
@@ -395,7 +421,7 @@ extern "C" int agatha_init(agatha_ctx **out, const agatha_config *cfg) {
         agatha_destroy(ctx);
         return AGATHA_ECUDA;
     }
-    if (c.max_pairs > 0) ensure_batch_buffers(ctx, c.max_pairs, 0, 0, true);
+    if (c.max_pairs > 0) slot_ensure(ctx, ctx->ledger, &ctx->main, c.max_pairs, 0, 0, true);
     *out = ctx;
     return AGATHA_OK;
 }
@@ -403,18 +429,12 @@ extern "C" int agatha_init(agatha_ctx **out, const agatha_config *cfg) {
 extern "C" void agatha_destroy(agatha_ctx *ctx) {
     if (!ctx) return;
     agatha_serve_stop(ctx, 0);
+    serve_free(ctx);
     cudaSetDevice(ctx->device);
     if (ctx->stream) cudaStreamSynchronize(ctx->stream);
-    for (auto &kv : ctx->graphs) cudaGraphExecDestroy(kv.second);
-    ctx->graphs.clear();
-    DevBuf *bufs[] = {&ctx->q_packed, &ctx->t_packed, &ctx->q_off, &ctx->t_off, &ctx->q_len,
-                      &ctx->t_len, &ctx->out, &ctx->order, &ctx->wide_order, &ctx->ovf_list, &ctx->counters,
-                      &ctx->hist, &ctx->desc};
-    for (DevBuf *b : bufs) b->release();
+    slot_release(ctx->ledger, &ctx->main);
     if (ctx->ev_k0) cudaEventDestroy(ctx->ev_k0);
     if (ctx->ev_k1) cudaEventDestroy(ctx->ev_k1);
-    if (ctx->h_desc) cudaFreeHost(ctx->h_desc);
-    if (ctx->h_counters) cudaFreeHost(ctx->h_counters);
     if (ctx->stream) cudaStreamDestroy(ctx->stream);
     delete ctx;
 }
@@ -463,31 +483,32 @@ extern "C" int agatha_align_batch(agatha_ctx *ctx, const agatha_batch *batch,
         // unbanded device batch: pairs wider than the warp kernel go to the block kernel
         lp.wide_w = plain_kernel_max_w();
     }
-    if ((rc = ensure_batch_buffers(ctx, n, batch->q_words, batch->t_words, !dev))) return rc;
+    Slot *sl = &ctx->main;
+    if ((rc = slot_ensure(ctx, ctx->ledger, sl, n, batch->q_words, batch->t_words, !dev))) return rc;
 
-    DevBatch *d = ctx->h_desc;
+    DevBatch *d = sl->h_desc;
     // the previous call's descriptor upload must be finished before it is rewritten
-    cudaStreamSynchronize(ctx->last_desc_stream ? ctx->last_desc_stream : s);
+    cudaStreamSynchronize(sl->last_stream ? sl->last_stream : s);
     if (!dev) {
         const int64_t qw = batch->q_words, tw = batch->t_words;
-        if (qw > 0 && (e = cudaMemcpyAsync(ctx->q_packed.ptr, batch->q_packed, qw * 4,
+        if (qw > 0 && (e = cudaMemcpyAsync(sl->q_packed.ptr, batch->q_packed, qw * 4,
                                            cudaMemcpyHostToDevice, s)) != cudaSuccess)
             return cuda_fail(ctx, e, "copy q_packed");
-        if (tw > 0 && (e = cudaMemcpyAsync(ctx->t_packed.ptr, batch->t_packed, tw * 4,
+        if (tw > 0 && (e = cudaMemcpyAsync(sl->t_packed.ptr, batch->t_packed, tw * 4,
                                            cudaMemcpyHostToDevice, s)) != cudaSuccess)
             return cuda_fail(ctx, e, "copy t_packed");
-        if ((e = cudaMemcpyAsync(ctx->q_off.ptr, batch->q_off, n * 8, cudaMemcpyHostToDevice, s)) ||
-            (e = cudaMemcpyAsync(ctx->t_off.ptr, batch->t_off, n * 8, cudaMemcpyHostToDevice, s)) ||
-            (e = cudaMemcpyAsync(ctx->q_len.ptr, batch->q_len, n * 4, cudaMemcpyHostToDevice, s)) ||
-            (e = cudaMemcpyAsync(ctx->t_len.ptr, batch->t_len, n * 4, cudaMemcpyHostToDevice, s)))
+        if ((e = cudaMemcpyAsync(sl->q_off.ptr, batch->q_off, n * 8, cudaMemcpyHostToDevice, s)) ||
+            (e = cudaMemcpyAsync(sl->t_off.ptr, batch->t_off, n * 8, cudaMemcpyHostToDevice, s)) ||
+            (e = cudaMemcpyAsync(sl->q_len.ptr, batch->q_len, n * 4, cudaMemcpyHostToDevice, s)) ||
+            (e = cudaMemcpyAsync(sl->t_len.ptr, batch->t_len, n * 4, cudaMemcpyHostToDevice, s)))
             return cuda_fail(ctx, e, "copy batch arrays");
-        d->q_packed = (const uint32_t *)ctx->q_packed.ptr;
-        d->t_packed = (const uint32_t *)ctx->t_packed.ptr;
-        d->q_off = (const int64_t *)ctx->q_off.ptr;
-        d->t_off = (const int64_t *)ctx->t_off.ptr;
-        d->q_len = (const int32_t *)ctx->q_len.ptr;
-        d->t_len = (const int32_t *)ctx->t_len.ptr;
-        d->out = (agatha_result *)ctx->out.ptr;
+        d->q_packed = (const uint32_t *)sl->q_packed.ptr;
+        d->t_packed = (const uint32_t *)sl->t_packed.ptr;
+        d->q_off = (const int64_t *)sl->q_off.ptr;
+        d->t_off = (const int64_t *)sl->t_off.ptr;
+        d->q_len = (const int32_t *)sl->q_len.ptr;
+        d->t_len = (const int32_t *)sl->t_len.ptr;
+        d->out = (agatha_result *)sl->out.ptr;
     } else {
         d->q_packed = batch->q_packed;
         d->t_packed = batch->t_packed;
@@ -500,23 +521,25 @@ extern "C" int agatha_align_batch(agatha_ctx *ctx, const agatha_batch *batch,
     d->q_words = batch->q_words;
     d->t_words = batch->t_words;
     d->n_pairs = n;
-    fill_desc(ctx, d, p, lp);
-    if ((e = cudaMemcpyAsync(ctx->d_desc, d, sizeof(DevBatch), cudaMemcpyHostToDevice, s)) != cudaSuccess)
+    fill_desc(sl, d, p, lp, sl->order.ptr, sl->wide_order.ptr, sl->ovf_list.ptr);
+    if ((e = cudaMemcpyAsync(sl->d_desc, d, sizeof(DevBatch), cudaMemcpyHostToDevice, s)) != cudaSuccess)
         return cuda_fail(ctx, e, "copy descriptor");
-    ctx->last_desc_stream = s;
-    if ((e = run_plan(ctx, lp, s)) != cudaSuccess) return cuda_fail(ctx, e, "launch");
+    sl->last_stream = s;
+    if ((e = slot_run(ctx, sl, lp, s, ctx->timing ? ctx->ev_k0 : nullptr, ctx->timing ? ctx->ev_k1 : nullptr)) !=
+        cudaSuccess)
+        return cuda_fail(ctx, e, "launch");
     ctx->timed_once = true;
-    if ((e = cudaMemcpyAsync(ctx->h_counters, ctx->counters.ptr, CTR_COUNT * sizeof(int32_t),
+    if ((e = cudaMemcpyAsync(sl->h_counters, sl->counters.ptr, CTR_COUNT * sizeof(int32_t),
                              cudaMemcpyDeviceToHost, s)) != cudaSuccess)
         return cuda_fail(ctx, e, "copy counters");
     if (!dev) {
-        if ((e = cudaMemcpyAsync(out, ctx->out.ptr, n * sizeof(agatha_result), cudaMemcpyDeviceToHost,
+        if ((e = cudaMemcpyAsync(out, sl->out.ptr, n * sizeof(agatha_result), cudaMemcpyDeviceToHost,
                                  s)) != cudaSuccess)
             return cuda_fail(ctx, e, "copy results");
     }
     if (flags & AGATHA_ASYNC) return AGATHA_OK;
     if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return cuda_fail(ctx, e, "synchronize");
-    if (ctx->h_counters[CTR_ERR] != DEV_ERR_NONE)
+    if (sl->h_counters[CTR_ERR] != DEV_ERR_NONE)
         return set_error(ctx, AGATHA_EINVAL, "a pair has a bad length, offset or score range");
     return AGATHA_OK;
 }

@@ -22,11 +22,17 @@ struct ServeState;
 
 namespace agatha {
 
+// Device bytes a context's own buffers hold, against its budget.
+struct Ledger {
+    int64_t budget = 0;            // 0: no limit
+    int64_t held = 0;
+};
+
 struct DevBuf {
     void *ptr = nullptr;
     size_t cap = 0;
-    int ensure(agatha_ctx *ctx, size_t need);
-    void release();
+    int ensure(agatha_ctx *ctx, Ledger &ledger, size_t need);
+    void release(Ledger &ledger);
 };
 
 struct BatchShape {
@@ -36,19 +42,34 @@ struct BatchShape {
     int32_t max_w_warp = 0;
 };
 
+using PlanKey = std::tuple<int, int, int, int, int32_t, int, int>;
+
 struct LaunchPlan {
     int64_t n = 0;
     int plain = 0, sort = 1, fast = 1, use_graph = 1;
     int C = 16;
     int32_t warp_w_max = 0;
     int warp_blocks = 0;
-    int lane16 = 0, C16 = 0, warp16_blocks = 0;
+    int lane16 = 0, C16 = 0, warp16_blocks = 0, minb16 = 4;
     int32_t wide_w = 0;         // > 0: pairs wider than the warp kernel exist
     int32_t plain_w = 0;
     int64_t plain_blocks = 0;
-    std::tuple<int, int, int, int, int32_t, int> key() const {
-        return std::make_tuple(plain, C + 100 * C16 * lane16, sort, fast, wide_w, warp_blocks);
+    PlanKey key() const {
+        return std::make_tuple(plain, C + 100 * C16 * lane16, sort, fast, wide_w, warp_blocks, minb16);
     }
+};
+
+// Everything one batch needs on the device: input copies (host batches),
+// results, scheduling scratch, the descriptor the kernels read, and the
+// CUDA graphs captured for this slot (they bake in the slot's addresses).
+struct Slot {
+    DevBuf q_packed, t_packed, q_off, t_off, q_len, t_len, out, order, wide_order, ovf_list,
+        counters, hist, desc;
+    DevBatch *d_desc = nullptr;
+    DevBatch *h_desc = nullptr;       // pinned staging of the descriptor
+    int32_t *h_counters = nullptr;    // pinned copy of the counters after a batch
+    cudaStream_t last_stream = nullptr;
+    std::map<std::tuple<int, PlanKey>, cudaGraphExec_t> graphs;
 };
 
 int set_error(agatha_ctx *ctx, int code, const char *fmt, ...);
@@ -56,7 +77,26 @@ int cuda_fail(agatha_ctx *ctx, cudaError_t e, const char *what);
 int normalise_params(const agatha_params *in, DevParams *out);
 int validate_host_batch(agatha_ctx *ctx, const agatha_batch *b, const DevParams &p, BatchShape *shape);
 int pick_slots_per_lane(int32_t w);
+int pick_slots16(int32_t w);
 int warp_occupancy(int C);
+int warp16_occupancy(int C);
+
+int slot_init(agatha_ctx *ctx, Ledger &ledger, Slot *s);
+void slot_release(Ledger &ledger, Slot *s);
+int slot_ensure(agatha_ctx *ctx, Ledger &ledger, Slot *s, int64_t n, int64_t q_words,
+                int64_t t_words, bool copy_inputs);
+int make_plan(agatha_ctx *ctx, const DevParams &p, const BatchShape &shape, uint32_t flags,
+              LaunchPlan *lp);
+// Fill the scheduling fields of a descriptor; order/wide_order/ovf_list are
+// device arrays of n_pairs int32 each.
+void fill_desc(const Slot *s, DevBatch *d, const DevParams &p, const LaunchPlan &lp, void *order,
+               void *wide_order, void *ovf_list);
+// Enqueue validation, ordering and the alignment kernels of the batch whose
+// descriptor is in s->d_desc; ev0/ev1 (may be null) bracket the kernels.
+cudaError_t slot_run(agatha_ctx *ctx, Slot *s, const LaunchPlan &lp, cudaStream_t st,
+                     cudaEvent_t ev0, cudaEvent_t ev1);
+// Stop and free the context's server, if any (serve.cu).
+void serve_free(agatha_ctx *ctx);
 
 }  // namespace agatha
 
@@ -65,21 +105,12 @@ struct agatha_ctx {
     int n_sm = 0;
     int cc_major = 0, cc_minor = 0;
     cudaStream_t stream = nullptr;
-    cudaStream_t last_desc_stream = nullptr;
-    int64_t mem_budget = 0;
-    int64_t mem_held = 0;
-    int64_t fail_alloc_after = -1;     // test hook: fail the n-th next allocation
+    agatha::Ledger ledger;
     std::string tune_cache_path;
     std::mutex mu;                     // serialises align_batch calls
     std::mutex err_mu;
     std::string last_error, last_error_copy;
-    agatha::DevBuf q_packed, t_packed, q_off, t_off, q_len, t_len, out, order, wide_order,
-        ovf_list, counters, hist, desc;
-    agatha::DevBatch *d_desc = nullptr;
-    agatha::DevBatch *h_desc = nullptr;
-    int32_t *h_counters = nullptr;
-    bool graphs_stale = false;
-    std::map<std::tuple<int, std::tuple<int, int, int, int, int32_t, int>>, cudaGraphExec_t> graphs;
+    agatha::Slot main;                 // buffers of agatha_align_batch
     ServeState *serve = nullptr;
     bool timing = false;               // AGATHA_CFG_TIMING
     bool timed_once = false;

@@ -1,0 +1,104 @@
+"""Serving benchmark: Poisson request arrivals into the continuous-batching
+loop (``agatha_serve_*``), one JSON line per arrival rate.
+
+Requests carry 1-512 pairs drawn uniformly from the ONT-like mix (20,000
+pairs, w=500, Z-drop 400); the server has a 16 GB arena.  At each rate the
+arrivals run until 2,000 requests or 10 s of arrivals, whichever comes first
+(at least 50 requests).  Latency = completion - scheduled arrival, where
+completion is seen by a thread that waits on the tickets in submission order
+(a request that completes before an earlier one is counted when the earlier
+one is done, so tail figures are, if anything, pessimistic).  The library's
+own submit-to-completion percentiles are reported beside them.
+
+    python -m paper_2403_06478_gb300.serve_bench [--rates 10,100,1000] [--budget-gb 16]
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import threading
+import time
+
+import numpy as np
+
+from . import agatha as A
+from . import build as B
+from . import workload as W
+
+
+def _point(ctx, pool_pb, pool, rate, args, rng):
+    n_req = int(max(50, min(args.max_requests, round(rate * args.max_seconds))))
+    reqs = W.poisson_requests(rng, rate, n_req, pool.n_pairs, args.max_pairs)
+    # each request references the pool's packed streams: submission copies
+    # only the words its pairs touch
+    batches = [A.PackedBatch(pool_pb.q_packed, pool_pb.t_packed, pool_pb.q_off[r.pair_idx],
+                             pool_pb.t_off[r.pair_idx], pool_pb.q_len[r.pair_idx],
+                             pool_pb.t_len[r.pair_idx]) for r in reqs]
+    srv = A.Server(ctx, mem_budget_bytes=int(args.budget_gb * (1 << 30)),
+                   max_inflight=args.max_inflight, max_batch_pairs=args.max_batch_pairs,
+                   linger_us=args.linger_us)
+    tickets = [None] * n_req
+    done_at = [0.0] * n_req
+    submitted = threading.Semaphore(0)
+
+    def waiter():
+        for i in range(n_req):
+            submitted.acquire()
+            srv.wait(tickets[i])
+            done_at[i] = time.perf_counter()
+
+    th = threading.Thread(target=waiter)
+    th.start()
+    t0 = time.perf_counter()
+    for i, r in enumerate(reqs):
+        delay = t0 + r.arrival_s - time.perf_counter()
+        if delay > 0:
+            time.sleep(delay)
+        tickets[i] = srv.submit(batches[i], pool.scoring)
+        submitted.release()
+    th.join()
+    t_end = max(done_at)
+    st = srv.stats()
+    srv.stop(drain=True)
+    lat = np.array([done_at[i] - (t0 + reqs[i].arrival_s) for i in range(n_req)]) * 1e3
+    pairs = int(sum(len(r.pair_idx) for r in reqs))
+    wall = t_end - t0
+    return {
+        "rate_req_s": rate, "requests": n_req, "pairs": pairs,
+        "offered_pairs_per_s": pairs / reqs[-1].arrival_s,
+        "pairs_per_s": pairs / wall, "gcups": st["cells_done"] / wall / 1e9,
+        "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
+        "lib_p50_ms": st["p50_latency_ms"], "lib_p99_ms": st["p99_latency_ms"],
+        "launches": st["launches"], "busy_s": st["busy_seconds"], "wall_s": wall,
+        "peak_bytes_in_flight": st["peak_bytes_in_flight"],
+    }
+
+
+def main(argv=None):
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--rates", default="10,20,50,100,200,500,1000,2000")
+    ap.add_argument("--max-requests", type=int, default=2000)
+    ap.add_argument("--max-seconds", type=float, default=10.0)
+    ap.add_argument("--max-pairs", type=int, default=512)
+    ap.add_argument("--budget-gb", type=float, default=16.0)
+    ap.add_argument("--max-inflight", type=int, default=2)
+    ap.add_argument("--max-batch-pairs", type=int, default=8192)
+    ap.add_argument("--linger-us", type=int, default=0)
+    ap.add_argument("--device", type=int, default=0)
+    args = ap.parse_args(argv)
+    B.build()
+    pool = W.make_config("ont")
+    pool_pb = A.pack_batch(pool)
+    ctx = A.Context(args.device)
+    rng = np.random.default_rng(W.SEED_BASE + 5)
+    for rate in [float(x) for x in args.rates.split(",")]:
+        line = _point(ctx, pool_pb, pool, rate, args, rng)
+        line["config"] = {"workload": "serving: Poisson arrivals, 1-512 ONT-like pairs per request",
+                          "budget_gb": args.budget_gb, "max_inflight": args.max_inflight,
+                          "max_batch_pairs": args.max_batch_pairs, "linger_us": args.linger_us}
+        print(json.dumps(line), flush=True)
+    ctx.close()
+
+
+if __name__ == "__main__":
+    main()
