@@ -39,7 +39,11 @@ WORKLOAD = ("ont: 20000 pairs, query log-normal (median 5 kbp, sigma 0.8, clip 5
             "target 5% sub / 4% del / 3% ins, 10% divergent tails, a=2 b=4 q=4 e=2 q2=24 e2=1, "
             "w=500, zdrop=400")
 L2_FLUSH_BYTES = 512 << 20          # > 129 MB of L2
-OPS_PER_CELL_I32 = 13               # issued int32 lane-ops per cell, see the design doc
+# algorithmic integer lane-ops per band cell (substitution score 2, five-way
+# max 3, two gap openings 2, four gap add-max 4, max tracking 2); a packed
+# 16x2 lane op serves two cells
+OPS_PER_CELL_I32 = 13.0
+OPS_PER_CELL_I16X2 = 6.5
 CPU_SAMPLE_PAIRS = 6000
 REF_STEP_PAIRS = 300
 
@@ -111,14 +115,28 @@ def measured_peaks():
     return {"hbm_gbs": 6800.0, "sm_max_mhz": 2070.0}, "fallback"
 
 
-def traffic_from_profile():
-    """DRAM bytes per launch of the warp kernel from the committed ncu summary."""
-    path = os.path.join(ROOT, "profiles", "warp_kernel_ont_traffic.json")
+def traffic_from_profile(kernel):
+    """DRAM bytes per full-size launch of the dominant kernel, from the
+    committed ncu summary (null if it was taken on another kernel build)."""
+    path = os.path.join(ROOT, "profiles", "warp16_kernel_ont_traffic.json")
     if not os.path.exists(path):
         return None
     with open(path) as fh:
         d = json.load(fh)
+    if d.get("kernel") != kernel or d.get("kernel_digest") != _kernel_digest():
+        return None
     return d.get("dram_bytes_per_launch")
+
+
+def _kernel_digest():
+    """Digest of the 16-bit kernel's sources: a traffic figure is only valid
+    for the build it was measured on."""
+    import hashlib
+    h = hashlib.sha256()
+    for f in ("kernel_warp16.cuh", "kernel_warp16_c16.cu", "agatha_dev.cuh"):
+        with open(os.path.join(ROOT, "paper_2403_06478_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
 
 
 def cpu_baseline(batch, n_sample: int, seed: int = 7):
@@ -304,13 +322,22 @@ def main():
     sm_max_mhz = float(peaks.get("sm_max_mhz", 2070.0))
     int_peak = n_sm * 128 * sm_max_mhz * 1e6 / 1e12         # Tops/s of int32 lanes
     k_ms = statistics.mean(kern_ms)
-    achieved = cells * OPS_PER_CELL_I32 / (k_ms / 1e3) / 1e12
+    lane16 = res["lane16"].astype(bool)
+    cells16 = int(res["cells"][lane16].sum())
+    ops = cells16 * OPS_PER_CELL_I16X2 + (cells - cells16) * OPS_PER_CELL_I32
+    achieved = ops / (k_ms / 1e3) / 1e12
+    kernel = "warp16_align_kernel<16>" if cells16 * 2 > cells else "warp_align_kernel<16>"
+    # kernels per step: prep classify/scan/scatter, the warp kernel and, with
+    # 16-bit lanes, the int32 kernel over the (usually empty) overflow list
+    launches_per_step = 3 + (2 if lane16.any() else 1)
     line = {
         "metric": METRIC, "value": round(value, 3), "unit": "GCUPS", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": round(tot_ms / args.steps, 3), "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "int32", "data": "synthetic",
+        "vs_baseline": None, "dtype": "int16x2" if cells16 * 2 > cells else "int32",
+        "data": "synthetic",
         "config": {"workload": WORKLOAD, "pairs_per_gpu": n, "cells_per_step": cells,
+                   "pairs_on_16bit_lanes": int(lane16.sum()),
                    "l2": "flushed between steps (512 MB write)", "inputs": "resident in HBM"},
         "pairs_per_s": round(all_pairs * args.steps / (tot_ms / 1e3), 1),
         "plain": {"value": round(all_cells / (statistics.mean(plain_ms) / 1e3) / 1e9, 3)
@@ -323,11 +350,11 @@ def main():
         "e2e": {"value": round(e2e_value, 3), "unit": "GCUPS", "h2d_bytes_per_step": int(h2d),
                 "d2h_bytes_per_step": int(d2h), "bit_exact": e2e_exact,
                 "ms_per_step": round(e2e_tot / args.steps, 3)},
-        "gpu_launches": 4 * args.steps,
+        "gpu_launches": launches_per_step * args.steps,
         "roofline": {"bound": "alu", "achieved": round(achieved, 3),
                      "peak": round(int_peak, 3), "unit": "Tops/s", "frac": round(achieved / int_peak, 4),
-                     "traffic": traffic_from_profile(), "kernel": "warp_align_kernel",
-                     "kernel_ms": round(k_ms, 3), "ops_per_cell": OPS_PER_CELL_I32,
+                     "traffic": traffic_from_profile(kernel), "kernel": kernel,
+                     "kernel_ms": round(k_ms, 3), "ops_per_cell": round(ops / max(cells, 1), 3),
                      "peak_basis": f"{n_sm} SMs x 128 int32 lanes x {sm_max_mhz:.0f} MHz ({peak_kind})"},
         "clocks": clocks,
     }
