@@ -297,17 +297,9 @@ def main():
     d2h = n * 48 + 32
 
     # aggregate over ranks: units all ranks processed / the slowest rank's time
-    tot_ms, e2e_tot = sum(step_ms), sum(e2e_ms)
-    agg = torch.tensor([float(cells), tot_ms, e2e_tot, float(n)], dtype=torch.float64, device="cuda")
-    if dist is not None:
-        cells_t = agg[[0, 3]].clone()
-        dist.all_reduce(cells_t, op=dist.ReduceOp.SUM)
-        times_t = agg[[1, 2]].clone()
-        dist.all_reduce(times_t, op=dist.ReduceOp.MAX)
-        all_cells, all_pairs = float(cells_t[0]), float(cells_t[1])
-        tot_ms, e2e_tot = float(times_t[0]), float(times_t[1])
-    else:
-        all_cells, all_pairs = float(cells), float(n)
+    from paper_2403_06478_gb300 import shard as S
+    (all_cells, all_pairs), (tot_ms, e2e_tot) = S.reduce_step_stats(
+        [cells, n], [sum(step_ms), sum(e2e_ms)], device="cuda")
     value = all_cells * args.steps / (tot_ms / 1e3) / 1e9
     e2e_value = all_cells * args.steps / (e2e_tot / 1e3) / 1e9
 
