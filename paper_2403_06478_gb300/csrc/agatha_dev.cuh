@@ -78,6 +78,15 @@ __host__ __device__ inline int32_t effective_w(int32_t w, int32_t tlen, int32_t 
     return (w < 0 || w > m) ? m : w;
 }
 
+// The largest change of a score from one anti-diagonal to the next: the
+// 16-bit lanes are sized from it.
+__host__ __device__ inline int32_t step_change_max(const DevParams &p) {
+    int32_t d = p.a > p.b ? p.a : p.b;
+    d = d > p.q + p.e ? d : p.q + p.e;
+    d = d > p.q2 + p.e2 ? d : p.q2 + p.e2;
+    return d > 0 ? d : 1;
+}
+
 // One packed word of a stream, zero outside it (reads are clamped).
 __device__ __forceinline__ uint32_t load_word(const uint32_t *__restrict__ p, int64_t n_words,
                                               int64_t i) {

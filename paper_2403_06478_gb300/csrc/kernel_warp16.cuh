@@ -61,13 +61,6 @@ __device__ __forceinline__ uint32_t mux(uint32_t m, uint32_t x, uint32_t y) {
     return (m & x) | (~m & y);
 }
 
-__host__ __device__ inline int32_t step_change_max(const DevParams &p) {
-    int32_t d = p.a > p.b ? p.a : p.b;
-    d = d > p.q + p.e ? d : p.q + p.e;
-    d = d > p.q2 + p.e2 ? d : p.q2 + p.e2;
-    return d > 0 ? d : 1;
-}
-
 template <int C>
 struct WarpPair16 {
     static_assert(C == 8 || C == 16, "16-bit lanes use 8 or 16 slots per lane");

@@ -13,7 +13,6 @@
 #include <vector>
 
 #include "agatha_dev.cuh"
-#include "kernel_warp16.cuh"
 #include "runtime.h"
 
 using namespace agatha;
@@ -340,7 +339,7 @@ int make_plan(agatha_ctx *ctx, const DevParams &p, const BatchShape &shape, uint
     const int occ = warp_occupancy(lp->C);
     lp->warp_blocks = ctx->n_sm * occ;
     // 16-bit packed lanes when the band fits and one anti-diagonal changes a
-    // score by at most 64 (see kernel_warp16.cuh)
+    // score by at most 64 (the headroom the 16-bit kernel's rebasing keeps)
     lp->C16 = pick_slots16(shape.max_w_all);
     lp->lane16 = !(flags & AGATHA_FORCE32) && lp->C16 > 0 && step_change_max(p) <= 64 && !lp->wide_w;
     if (lp->lane16) {
