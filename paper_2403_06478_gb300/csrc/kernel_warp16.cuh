@@ -22,9 +22,10 @@
 //     the current anti-diagonal maximum (stored at OFF) and the warp checks,
 //     exactly, that every score of a band cell is at least (K+3)D above NEG.
 //     Between rebases scores then stay in [NEG + 2D, OFF + (K+1)D], clear of
-//     NEG and of 0xFFFF.  A pair that fails the check (a score spread of more
-//     than ~45,000 inside the band) is handed to the int32 kernel, which
-//     recomputes it from the start; no 16-bit result is written for it.
+//     NEG and of 0xFFFF.  K is as large as a score spread of 32,768 inside
+//     the band allows (570 anti-diagonals for D = 25).  A pair that fails the
+//     check is handed to the int32 kernel, which recomputes it from the
+//     start; no 16-bit result is written for it.
 //   - Real scores never come near 0 or 0xFFFF, so packed 32-bit adds and
 //     subtracts never carry or borrow across the two halves (a borrow out of a
 //     slot beyond the band can only reach the high half, which is then beyond
@@ -48,11 +49,28 @@
 namespace agatha {
 
 constexpr uint32_t U_NEG = 0x1000u;     // minus infinity of the 16-bit lanes
-constexpr int32_t U_K = 128;            // anti-diagonals between rebases, at most
+constexpr int32_t U_SPREAD = 32768;     // score spread inside the band the lanes keep
+
+// Anti-diagonals between rebases for a step change of at most D: as many as
+// leave U_SPREAD between the lowest band score allowed and the rebased maximum.
+__host__ __device__ inline int32_t rebase_interval(int32_t D) {
+    int32_t k = (int32_t)(0xffff - U_NEG - U_SPREAD) / (2 * D) - 3;
+    k = k < 16 ? 16 : (k > 4096 ? 4096 : k);
+    return k & ~1;
+}
 
 __device__ __forceinline__ uint32_t prmt(uint32_t a, uint32_t b, uint32_t sel) {
     uint32_t d;
     asm("prmt.b32 %0, %1, %2, %3;" : "=r"(d) : "r"(a), "r"(b), "r"(sel));
+    return d;
+}
+// Sign of each 16-bit half of (a - b) replicated over the half, computed
+// where it is used: a mask that is cheaper to recompute than to keep in a
+// register across the anti-diagonal loop.
+__device__ __forceinline__ uint32_t half_sign_of_diff(uint32_t a, uint32_t b) {
+    uint32_t d;
+    asm volatile("{\n\t.reg .b32 t;\n\tsub.u32 t, %1, %2;\n\tprmt.b32 %0, t, 0, 0xbb99;\n\t}"
+                 : "=r"(d) : "r"(a), "r"(b));
     return d;
 }
 
@@ -60,6 +78,10 @@ __device__ __forceinline__ uint32_t prmt(uint32_t a, uint32_t b, uint32_t sel) {
 __device__ __forceinline__ uint32_t mux(uint32_t m, uint32_t x, uint32_t y) {
     return (m & x) | (~m & y);
 }
+
+struct Cold16 {
+    int32_t mqe, mqe_t, mte, mte_q, gscore;
+};
 
 template <int C>
 struct WarpPair16 {
@@ -76,22 +98,30 @@ struct WarpPair16 {
     // odd one.  Gap states leaving the last anti-diagonal: Eo to (t+1,q), Fo
     // to (t,q+1), E2o/F2o the same for the second gap piece.
     uint32_t Hev[P], Hod[P], Eo[P], E2o[P], Fo[P], F2o[P];
-    uint32_t DM[P];        // 0xFFFF halves: slot beyond the band (j > w)
-    uint32_t DM0odd;       // DM[0] plus slot 0 of lane 0 (outside on odd anti-diagonals)
+    // slots beyond the band (j > w): local slots k0.. of this lane, held as
+    // (k0 - 1) in both halves so that dead_mask() is one add and one prmt
+    uint32_t DF2;
     // base windows (2 bits per slot): Tw field jl = T[B + j0 + jl],
     // Qw field jl = Q[r - B - j0 - jl]
     uint32_t Tw, Qw, Tpf, Qpf;
     int32_t tcnt, qcnt;
     int64_t tpos, qpos;
     // relative scores
-    int32_t base, Dp, LOWCHK, OFF, since, last_m;
+    int32_t base, Dp, LOWCHK, OFF, last_m;
+    int32_t until_rebase;  // anti-diagonals left before the next rebase
+    int32_t kint;          // the rebase interval K
     bool ovf;
     // packed constants
     uint32_t A2, NB2, OEp, DOEp, Ep, E2p, NEp, NE2p, NEGp, L0LO, L31HI;
     // bookkeeping (uniform across the warp)
-    int32_t gmax, gt, gq, mqe, mqe_t, mte, mte_q, gscore;
+    int32_t gmax, gt, gq;
     int64_t cells;
     int32_t zdropped;
+    // results only the table edges change, kept in shared memory (written by
+    // lane 0) so they hold no registers through the bulk loop
+    Cold16 &cold;
+
+    __device__ explicit WarpPair16(Cold16 &c) : cold(c) {}
 
     __device__ __forceinline__ int32_t to_true(int32_t u) const { return u - OFF + base; }
     __device__ __forceinline__ int32_t to_u(int32_t v) const { return v - base + OFF; }
@@ -152,6 +182,18 @@ struct WarpPair16 {
     __device__ __forceinline__ static uint32_t slot_bit(int32_t jl) {
         if (jl < 0 || jl >= C) return 0u;
         return jl < P ? (1u << jl) : (1u << (16 + jl - P));
+    }
+
+    // 0xFFFF halves of register p whose slot lies beyond the band: the half
+    // (k0 - 1 - slot) is negative exactly there (a borrow out of the low half
+    // only reaches a high half that is beyond the band as well)
+    __device__ __forceinline__ uint32_t dead_mask(int p) const {
+        return half_sign_of_diff(DF2, (uint32_t)p | ((uint32_t)(p + P) << 16));
+    }
+    // the same plus slot 0 of lane 0, outside the band on odd anti-diagonals
+    template <bool ODD>
+    __device__ __forceinline__ uint32_t dead_mask_r(int p) const {
+        return (ODD && p == 0) ? (dead_mask(0) | L0LO) : dead_mask(p);
     }
 
     // ------------------------------------------------------- Eq. 4-7 test
@@ -287,7 +329,7 @@ struct WarpPair16 {
             const uint32_t H = __vmaxu2(__vimax3_u16x2(__viaddmax_u16x2(Hd[p], s2, Ein), Fin, E2in),
                                         F2in);
             if constexpr (!MASKED) {
-                const uint32_t dead = (ODD && p == 0) ? DM0odd : DM[p];
+                const uint32_t dead = dead_mask_r<ODD>(p);
                 const uint32_t hoe = mux(dead, NEGp, H - OEp);
                 const uint32_t hoe2 = hoe - DOEp;
                 // per-half add of -e (wraps within the half) then max: one op each
@@ -315,32 +357,33 @@ struct WarpPair16 {
             }
         }
         if constexpr (!MASKED) {
-            cells += w + 1 - (ODD ? 1 : 0);
-            return anti_diagonal_max<ODD>(r, B, lmax, Hd, [&](int p) {
-                return (ODD && p == 0) ? DM0odd : DM[p];
-            });
+            // (the band cells of bulk anti-diagonals are counted by run())
+            return anti_diagonal_max<ODD>(r, B, lmax, Hd, [&](int p) { return dead_mask_r<ODD>(p); });
         } else {
             if (__any_sync(FULL, ovf)) { ovf = true; return true; }
             if (r < 0) return false;
             cells += en - st + 1;
             // best score on the last target row / the last query column
+            bool set_gs = false;
+            int32_t gs = K_NEG_OUT;
             if (te_real) {
-                const int32_t tv = __reduce_max_sync(FULL, (int32_t)max(tmax & 0xffffu, tmax >> 16));
-                if (to_true(tv) > mte) { mte = to_true(tv); mte_q = r - (tlen - 1); }
-                if (r == last_r) gscore = to_true(tv);     // set below unless Z-drop stops r
+                const int32_t tv = to_true(
+                    __reduce_max_sync(FULL, (int32_t)max(tmax & 0xffffu, tmax >> 16)));
+                if (tv > cold.mte && lane == 0) { cold.mte = tv; cold.mte_q = r - (tlen - 1); }
+                if (r == last_r) { gs = tv; set_gs = true; }   // kept unless Z-drop stops r
             }
             if (qe_real) {
-                const int32_t qv = __reduce_max_sync(FULL, (int32_t)max(qmax & 0xffffu, qmax >> 16));
-                if (to_true(qv) > mqe) { mqe = to_true(qv); mqe_t = r - (qlen - 1); }
+                const int32_t qv = to_true(
+                    __reduce_max_sync(FULL, (int32_t)max(qmax & 0xffffu, qmax >> 16)));
+                if (qv > cold.mqe && lane == 0) { cold.mqe = qv; cold.mqe_t = r - (qlen - 1); }
             }
-            const int32_t gs = gscore;
-            if (r == last_r) gscore = K_NEG_OUT;
+            __syncwarp();
             if (anti_diagonal_max<ODD>(r, B, lmax, Hd, [&](int p) {
                     return ~prmt(rb << (15 - p), 0, 0xbb99);
                 }))
                 return true;
-            if (r == last_r) gscore = gs;
-            if (++since >= U_K - 2) rebase(last_m, r);
+            if (set_gs && lane == 0) cold.gscore = gs;
+            if (--until_rebase <= 2) rebase(last_m, r);
             return ovf;
         }
     }
@@ -352,8 +395,8 @@ struct WarpPair16 {
         if (step<false, false>(r)) return 1;
         shift_q();
         if (step<true, false>(r + 1)) return 2;
-        since += 2;
-        if (since >= U_K - 2) {
+        until_rebase -= 2;
+        if (until_rebase <= 2) {
             rebase(last_m, r + 1);
             if (ovf) return 2;
         }
@@ -379,15 +422,16 @@ struct WarpPair16 {
     }
     // r: the last anti-diagonal computed (its gap states are in Eo..)
     __device__ __forceinline__ void rebase(int32_t m_u, int32_t r) {
-        since = 0;
+        until_rebase = kint;
         const int32_t delta = m_u - OFF;
         const int32_t low = LOWCHK - Dp + delta;
         const bool odd = ((r - w) & 1) != 0;
 #pragma unroll
         for (int p = 0; p < P; ++p) {
-            const uint32_t dm_odd = p == 0 ? DM0odd : DM[p];
-            const uint32_t dm_r = odd ? dm_odd : DM[p];       // slots of anti-diagonal r
-            rebase_reg(Hev[p], DM[p], delta, low);
+            const uint32_t dm = dead_mask(p);
+            const uint32_t dm_odd = p == 0 ? (dm | L0LO) : dm;
+            const uint32_t dm_r = odd ? dm_odd : dm;           // slots of anti-diagonal r
+            rebase_reg(Hev[p], dm, delta, low);
             rebase_reg(Hod[p], dm_odd, delta, low);
             rebase_reg(Eo[p], dm_r, delta, low);
             rebase_reg(E2o[p], dm_r, delta, low);
@@ -416,10 +460,11 @@ struct WarpPair16 {
         j0 = lane * C;
         last_r = tlen + qlen - 2;
         Dp = step_change_max(prm);
-        LOWCHK = (int32_t)U_NEG + (U_K + 3) * Dp;
-        OFF = 0xffff - (U_K + 3) * Dp;
+        kint = rebase_interval(Dp);
+        until_rebase = kint;
+        LOWCHK = (int32_t)U_NEG + (kint + 3) * Dp;
+        OFF = 0xffff - (kint + 3) * Dp;
         base = 0;
-        since = 0;
         last_m = OFF;
         ovf = false;
         A2 = ((uint32_t)prm.a & 0xffffu) * 0x10001u;
@@ -435,13 +480,18 @@ struct WarpPair16 {
         L31HI = lane == 31 ? 0xffff0000u : 0u;
 #pragma unroll
         for (int p = 0; p < P; ++p) {
-            const int32_t jlo = j0 + p, jhi = j0 + p + P;
-            DM[p] = (jlo > w ? 0x0000ffffu : 0u) | (jhi > w ? 0xffff0000u : 0u);
             Hev[p] = Hod[p] = Eo[p] = E2o[p] = Fo[p] = F2o[p] = NEGp;
         }
-        DM0odd = DM[0] | L0LO;
+        {
+            const int32_t k0 = min(max(w + 1 - j0, 0), C);     // first local slot beyond the band
+            DF2 = (uint32_t)(k0 - 1) * 0x10001u;
+        }
         gmax = 0; gt = -1; gq = -1;
-        mqe = K_NEG_OUT; mqe_t = -1; mte = K_NEG_OUT; mte_q = -1; gscore = K_NEG_OUT;
+        if (lane == 0) {
+            cold.mqe = K_NEG_OUT; cold.mqe_t = -1; cold.mte = K_NEG_OUT; cold.mte_q = -1;
+            cold.gscore = K_NEG_OUT;
+        }
+        __syncwarp();
         cells = 0; zdropped = 0;
 
         int32_t r = -2;
@@ -458,6 +508,7 @@ struct WarpPair16 {
         const int32_t L = min(tlen, qlen);
         const int32_t bulk_last = 2 * L - 3 - w;
         if (use_fast && !stop && r == w + 1) {
+            const int32_t r0 = r;
             while (r + 2 <= bulk_last) {
                 const int st = fast_pair(r + 1);
                 if (st) {
@@ -467,6 +518,10 @@ struct WarpPair16 {
                 }
                 r += 2;
             }
+            // every bulk anti-diagonal holds the whole band: w + 1 cells when
+            // (r - w) is even, w when it is odd; the first one is even
+            const int32_t nb = r - r0;
+            cells += (int64_t)(nb >> 1) * (2 * w + 1) + (int64_t)(nb & 1) * (w + 1);
         }
         while (!stop && r < last_r) {
             ++r;
@@ -476,8 +531,10 @@ struct WarpPair16 {
         if (ovf) return false;
         if (lane == 0) {
             agatha_result o;
+            const int32_t mqe = cold.mqe;
             o.max = gmax; o.te = gt; o.qe = gq;
-            o.gscore = gscore; o.mqe = mqe; o.mqe_t = mqe_t; o.mte = mte; o.mte_q = mte_q;
+            o.gscore = cold.gscore; o.mqe = mqe; o.mqe_t = cold.mqe_t; o.mte = cold.mte;
+            o.mte_q = cold.mte_q;
             o.cells = cells;
             o.zdropped = (uint8_t)zdropped;
             o.reach_end = (uint8_t)(!zdropped && mqe != K_NEG_OUT && mqe + prm.end_bonus > gmax);
@@ -492,6 +549,7 @@ struct WarpPair16 {
 template <int C>
 __global__ void __launch_bounds__(WARP_BLOCK_THREADS, 4)
 warp16_align_kernel(const DevBatch *__restrict__ d_batch, int32_t use_fast) {
+    __shared__ Cold16 cold[WARP_BLOCK_THREADS / 32];
     const DevBatch B = *d_batch;
     const int lane = threadIdx.x & 31;
     const bool sorted = B.order != nullptr;
@@ -503,7 +561,7 @@ warp16_align_kernel(const DevBatch *__restrict__ d_batch, int32_t use_fast) {
         if (k >= n_work) break;
         const int32_t pair = sorted ? B.order[k] : k;
         if (!sorted && (!pair_valid(B, pair) || !warp_takes(B, pair))) continue;
-        WarpPair16<C> wp;
+        WarpPair16<C> wp(cold[threadIdx.x >> 5]);
         if (!wp.run(B, pair, lane, use_fast != 0) && lane == 0) {
             const int32_t slot = atomicAdd(&B.counters[CTR_NOVF], 1);
             B.ovf_list[slot] = pair;
