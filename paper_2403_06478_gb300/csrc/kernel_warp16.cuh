@@ -43,6 +43,7 @@
 #pragma once
 
 #include <climits>
+#include <type_traits>
 
 #include "kernel_warp.cuh"
 
@@ -85,8 +86,14 @@ struct Cold16 {
 
 template <int C>
 struct WarpPair16 {
-    static_assert(C == 8 || C == 16, "16-bit lanes use 8 or 16 slots per lane");
+    static_assert(C == 8 || C == 16 || C == 24, "16-bit lanes use 8, 16 or 24 slots per lane");
     static constexpr int P = C / 2;
+    // a base window holds 2 bits per slot
+    using Win = typename std::conditional<(2 * C > 32), uint64_t, uint32_t>::type;
+    static constexpr Win WMASK = (Win)(((uint64_t)1 << (2 * C)) - 1);
+    // mismatch bits of a step: low-half slot p at bit 2p of lo, high-half
+    // slot p+P at bit 2p of hi (C = 24), or at bit 16+2p of lo (C <= 16)
+    struct Comb { uint32_t lo, hi; };
 
     const uint32_t *tp, *qp;
     int64_t tw, qw, toff, qoff;
@@ -103,7 +110,8 @@ struct WarpPair16 {
     uint32_t DF2;
     // base windows (2 bits per slot): Tw field jl = T[B + j0 + jl],
     // Qw field jl = Q[r - B - j0 - jl]
-    uint32_t Tw, Qw, Tpf, Qpf;
+    Win Tw, Qw;
+    uint32_t Tpf, Qpf;
     int32_t tcnt, qcnt;
     int64_t tpos, qpos;
     // relative scores
@@ -132,9 +140,13 @@ struct WarpPair16 {
         const int32_t B = frame(r);
         const int64_t tb = (int64_t)B + j0;
         const int64_t qb = (int64_t)r - B - j0;
-        const uint32_t mask = C == 16 ? 0xffffffffu : ((1u << (2 * C)) - 1);
-        Tw = load16(tp, tw, toff + tb) & mask;
-        Qw = rev2_32(load16(qp, qw, qoff + qb - C + 1)) >> (2 * (16 - C));
+        if constexpr (C <= 16) {
+            Tw = load16(tp, tw, toff + tb) & WMASK;
+            Qw = rev2_32(load16(qp, qw, qoff + qb - C + 1)) >> (2 * (16 - C));
+        } else {
+            Tw = load32(tp, tw, toff + tb) & WMASK;
+            Qw = rev2_64(load32(qp, qw, qoff + qb - C + 1)) >> (2 * (32 - C));
+        }
         tpos = tb + C;
         qpos = qb + 1;
         Tpf = load16(tp, tw, toff + tpos);
@@ -145,13 +157,12 @@ struct WarpPair16 {
         qcnt = 16;
     }
     __device__ __forceinline__ void shift_t() {
-        Tw = (Tw >> 2) | ((Tpf & 3u) << (2 * C - 2));
+        Tw = (Tw >> 2) | ((Win)(Tpf & 3u) << (2 * C - 2));
         Tpf >>= 2;
         if (--tcnt == 0) { Tpf = load16(tp, tw, toff + tpos); tpos += 16; tcnt = 16; }
     }
     __device__ __forceinline__ void shift_q() {
-        const uint32_t mask = C == 16 ? 0xffffffffu : ((1u << (2 * C)) - 1);
-        Qw = ((Qw << 2) | (Qpf & 3u)) & mask;
+        Qw = ((Qw << 2) | (Win)(Qpf & 3u)) & WMASK;
         Qpf >>= 2;
         if (--qcnt == 0) { Qpf = load16(qp, qw, qoff + qpos); qpos += 16; qcnt = 16; }
     }
@@ -159,12 +170,23 @@ struct WarpPair16 {
     __device__ __forceinline__ void advance(int32_t r) {
         if ((r - w) & 1) shift_q(); else shift_t();
     }
-    // mismatch bits: low-half slot p at bit 2p, high-half slot p+P at 16+2p
-    __device__ __forceinline__ uint32_t packed_mismatch() const {
-        const uint32_t x = Tw ^ Qw;
-        const uint32_t nm = (x | (x >> 1)) & 0x55555555u;    // slot jl at bit 2*jl
-        if constexpr (C == 16) return nm;
-        else return (nm & 0xffu) | ((nm & 0xff00u) << 8);
+    __device__ __forceinline__ Comb packed_mismatch() const {
+        const Win x = Tw ^ Qw;
+        const Win nm = (x | (x >> 1)) & (Win)0x5555555555555555ull;    // slot jl at bit 2*jl
+        if constexpr (C == 16) return {(uint32_t)nm, 0u};
+        else if constexpr (C == 8) return {((uint32_t)nm & 0xffu) | (((uint32_t)nm & 0xff00u) << 8), 0u};
+        else return {(uint32_t)(nm & 0xffffffu), (uint32_t)(nm >> 24)};
+    }
+    // 0xFFFF halves of register p where the slot's bases differ
+    __device__ __forceinline__ static uint32_t mismatch_mask(const Comb &c, int p) {
+        const int sh = 15 - 2 * p;
+        if constexpr (C <= 16) {
+            return prmt(c.lo << sh, 0, 0xbb99);
+        } else {
+            const uint32_t x = sh >= 0 ? c.lo << sh : c.lo >> -sh;
+            const uint32_t y = sh >= 0 ? c.hi << sh : c.hi >> -sh;
+            return prmt(x, y, 0xdd99);       // low half from bit 15 of x, high from bit 15 of y
+        }
     }
     // 0xFFFF halves of register p from lane bits (low half p at bit p, high at 16+p)
     template <int PP>
@@ -305,8 +327,8 @@ struct WarpPair16 {
             edge = mux(L31HI, inj, prmt(Fo[0], fR, 0x5432));
             edge2 = mux(L31HI, inj2, prmt(F2o[0], f2R, 0x5432));
         }
-        const uint32_t comb = packed_mismatch();
-        uint32_t lmax = 0, tmax = 0, qmax = 0;
+        const Comb comb = packed_mismatch();
+        uint32_t lmax = 0, tmax = 0, qmax = 0, pend = 0;
 #pragma unroll
         for (int i = 0; i < P; ++i) {
             const int p = ODD ? P - 1 - i : i;
@@ -323,7 +345,7 @@ struct WarpPair16 {
                 F2in = p < P - 1 ? F2o[p + 1] : edge2;
             }
             // substitution: mismatch bits of both halves replicated to 0xFFFF masks
-            const uint32_t mm = prmt(comb << (15 - 2 * p), 0, 0xbb99);
+            const uint32_t mm = mismatch_mask(comb, p);
             const uint32_t s2 = mux(mm, NB2, A2);
             // H = max(H(r-2) + s, E, F, E2, F2): add-max, 3-input max, max
             const uint32_t H = __vmaxu2(__vimax3_u16x2(__viaddmax_u16x2(Hd[p], s2, Ein), Fin, E2in),
@@ -338,7 +360,10 @@ struct WarpPair16 {
                 E2o[p] = __viaddmax_u16x2(E2in, NE2p, hoe2);
                 F2o[p] = __viaddmax_u16x2(F2in, NE2p, hoe2);
                 Hd[p] = H;
-                lmax = __vmaxu2(lmax, hoe);
+                // running maximum, two registers per 3-input max
+                if (i & 1) lmax = __vimax3_u16x2(lmax, pend, hoe);
+                else if (i == P - 1) lmax = __vmaxu2(lmax, hoe);
+                else pend = hoe;
             } else {
                 const uint32_t hoe = H - OEp;
                 const uint32_t hoe2 = hoe - DOEp;
@@ -546,8 +571,13 @@ struct WarpPair16 {
     }
 };
 
+// Resident blocks per SM the register budget is cut for: 4 blocks (128
+// registers a thread) up to 16 slots per lane, 3 (168) for 24.
 template <int C>
-__global__ void __launch_bounds__(WARP_BLOCK_THREADS, 4)
+constexpr int warp16_min_blocks() { return C <= 16 ? 4 : 3; }
+
+template <int C>
+__global__ void __launch_bounds__(WARP_BLOCK_THREADS, warp16_min_blocks<C>())
 warp16_align_kernel(const DevBatch *__restrict__ d_batch, int32_t use_fast) {
     __shared__ Cold16 cold[WARP_BLOCK_THREADS / 32];
     const DevBatch B = *d_batch;

@@ -163,17 +163,26 @@ static cudaError_t launch_warp(int C, const DevBatch *d, int blocks, cudaStream_
 }
 
 static cudaError_t launch_warp16(int C, const DevBatch *d, int blocks, cudaStream_t s, int fast) {
-    return C == 8 ? launch_warp16_c<8>(d, blocks, s, fast) : launch_warp16_c<16>(d, blocks, s, fast);
+    switch (C) {
+        case 8: return launch_warp16_c<8>(d, blocks, s, fast);
+        case 16: return launch_warp16_c<16>(d, blocks, s, fast);
+        default: return launch_warp16_c<24>(d, blocks, s, fast);
+    }
 }
 
 int warp16_occupancy(int C) {
-    return C == 8 ? occupancy_warp16_c<8>() : occupancy_warp16_c<16>();
+    switch (C) {
+        case 8: return occupancy_warp16_c<8>();
+        case 16: return occupancy_warp16_c<16>();
+        default: return occupancy_warp16_c<24>();
+    }
 }
 
 // Slots per lane of the 16-bit kernel for a band of half-width w (0: none).
 int pick_slots16(int32_t w) {
     if (w <= 32 * 8 - 1) return 8;
     if (w <= 32 * 16 - 1) return 16;
+    if (w <= 32 * 24 - 1) return 24;
     return 0;
 }
 

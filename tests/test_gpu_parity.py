@@ -99,10 +99,11 @@ def test_adversarial_pairs(ctx, si):
         _assert_same(got, ref, batch, f"adversarial[{si}]/{path}")
 
 
-def test_16bit_lanes_used_and_exact(ctx):
-    batch = W.make_config("ont", n_pairs=300)
+@pytest.mark.parametrize("name", ["small", "ont", "hifi", "skewed"])   # 8, 16, 16, 24 slots per lane
+def test_16bit_lanes_used_and_exact(ctx, name):
+    batch = W.make_config(name, n_pairs=300)
     got = A.agatha_align_batch(ctx, batch)
-    assert got["lane16"].mean() > 0.99          # w=500 and ONT scoring fit 16-bit lanes
+    assert got["lane16"].mean() > 0.99          # these bands and scorings fit 16-bit lanes
     ref = A.agatha_align_batch(ctx, batch, flags=A.AGATHA_FORCE32)
     assert (ref["lane16"] == 0).all()
     assert A.results_equal(got, ref).size == 0
