@@ -228,7 +228,7 @@ def main():
     batch = W.make_config("ont", seed=None if rank == 0 else W.SEED_BASE + 2 + 1000 * rank)
     pb = A.pack_batch(batch)
     n = pb.n_pairs
-    ctx = A.Context(local, timing=True)
+    ctx = A.Context(local, timing=True, autotune=True)
     # a dedicated stream: every launch, copy and timing event of the step sits on it
     stream = torch.cuda.Stream()
     torch.cuda.set_stream(stream)
@@ -237,6 +237,10 @@ def main():
            for k in ("q_packed", "t_packed", "q_off", "t_off", "q_len", "t_len")}
     out = torch.empty(n * 48, dtype=torch.uint8, device="cuda")
     flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device="cuda")
+
+    # the autotuner measures its variants on the first host batch of a scoring
+    ctx.align_host(pb, batch.scoring)
+    tuned = ctx.tune_variants(batch.scoring)
 
     def run_dev(flags):
         ctx.align_device(dev["q_packed"], dev["t_packed"], dev["q_off"], dev["t_off"], dev["q_len"],
@@ -318,10 +322,12 @@ def main():
     cells16 = int(res["cells"][lane16].sum())
     ops = cells16 * OPS_PER_CELL_I16X2 + (cells - cells16) * OPS_PER_CELL_I32
     achieved = ops / (k_ms / 1e3) / 1e12
-    kernel = "warp16_align_kernel<16>" if cells16 * 2 > cells else "warp_align_kernel<16>"
-    # kernels per step: prep classify/scan/scatter, the warp kernel and, with
-    # 16-bit lanes, the int32 kernel over the (usually empty) overflow list
-    launches_per_step = 3 + (2 if lane16.any() else 1)
+    kernel = "warp16_align_kernel<16, 4>" if cells16 * 2 > cells else "warp_align_kernel<16>"
+    # kernels per step: prep classify/scan/scatter, the warp kernel (one per
+    # length class when the autotuner split the queue) and, with 16-bit lanes,
+    # the int32 kernel over the (usually empty) overflow list
+    split = bool(tuned and tuned[4])
+    launches_per_step = 3 + (4 if split else 1) + (1 if lane16.any() else 0)
     line = {
         "metric": METRIC, "value": round(value, 3), "unit": "GCUPS", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup,
@@ -330,6 +336,8 @@ def main():
         "data": "synthetic",
         "config": {"workload": WORKLOAD, "pairs_per_gpu": n, "cells_per_step": cells,
                    "pairs_on_16bit_lanes": int(lane16.sum()),
+                   "autotune": None if tuned is None else
+                   {"class_variants": [A.VARIANT_NAMES[v] for v in tuned[:4]], "split": split},
                    "l2": "flushed between steps (512 MB write)", "inputs": "resident in HBM"},
         "pairs_per_s": round(all_pairs * args.steps / (tot_ms / 1e3), 1),
         "plain": {"value": round(all_cells / (statistics.mean(plain_ms) / 1e3) / 1e9, 3)

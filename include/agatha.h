@@ -65,10 +65,15 @@ extern "C" {
 #define AGATHA_NO_GRAPH    0x20u  /* launch directly, no CUDA graph replay    */
 #define AGATHA_EDGE_PATH_ONLY 0x40u /* batched kernel: run every anti-diagonal
                                      through the masked edge path (testing)  */
+#define AGATHA_REGS_HIGH   0x80u  /* 16-bit kernel at its larger register
+                                     budget (one resident block per SM less)  */
+#define AGATHA_NO_TUNE     0x100u /* ignore the autotuner for this call       */
 
 /* Flags for agatha_config.flags. */
 #define AGATHA_CFG_TIMING  0x1    /* record CUDA events around the main kernel
                                      of every batch (agatha_last_kernel_ms)   */
+#define AGATHA_CFG_AUTOTUNE 0x2   /* pick the kernel variant per length class
+                                     by measurement (see agatha_tune_variants) */
 
 typedef struct agatha_ctx agatha_ctx;
 
@@ -178,6 +183,24 @@ int agatha_pack_ascii(const char *ascii, int64_t n, uint32_t *out);
 /* Band cells of the whole table of a tlen x qlen pair with half-width w
  * (w < 0: unbanded): the work estimate used for scheduling. */
 int64_t agatha_band_cells(int32_t tlen, int32_t qlen, int32_t w);
+
+/* Autotuner.  With AGATHA_CFG_AUTOTUNE the batched path may split the
+ * ordered queue into four length classes by predicted band cells (the
+ * Section 4.5 model: >= 2^25, >= 2^23, >= 2^21, smaller) and launch one
+ * kernel per class.  The variant of each class (0: 16-bit lanes, 1: 16-bit
+ * lanes at the larger register budget, 2: int32 lanes) is measured the first
+ * time a host batch arrives for a scoring and band class, on up to 4096 of
+ * its pairs per class; a non-default variant must be 3% faster, and the split
+ * is kept only if the batch (up to 32768 of its pairs) runs 3% faster split
+ * than as one launch.  Choices are kept per context and in tune_cache_path (one line
+ * per key, read at agatha_init).  Every variant gives bit-identical results.
+ * agatha_tune_variants writes what was tuned for `params` (band half-width
+ * w_max: the widest effective band of the batches) into variants[0..4]: the
+ * four class variants, then 1 if the split is used.  AGATHA_OK, AGATHA_EAGAIN
+ * if not tuned yet, AGATHA_ENOTSUP if 16-bit lanes do not apply to these
+ * parameters (nothing to choose). */
+int agatha_tune_variants(agatha_ctx *ctx, const agatha_params *params, int32_t w_max,
+                         int32_t *variants);
 
 /* ---------------------------------------------------------------------- */
 /* Serving: continuous batching of alignment requests on one device.       */

@@ -36,8 +36,14 @@ AGATHA_NO_SORT = 0x08
 AGATHA_FORCE32 = 0x10
 AGATHA_NO_GRAPH = 0x20
 AGATHA_EDGE_PATH_ONLY = 0x40
+AGATHA_REGS_HIGH = 0x80
+AGATHA_NO_TUNE = 0x100
 
 AGATHA_CFG_TIMING = 0x1
+AGATHA_CFG_AUTOTUNE = 0x2
+
+# kernel variants the autotuner chooses between, per length class
+VARIANT_NAMES = ("int16x2", "int16x2-highreg", "int32")
 
 NEG_INF = -0x40000000
 
@@ -120,6 +126,8 @@ _SIGS = {
     "agatha_strerror": (ctypes.c_char_p, [ctypes.c_int]),
     "agatha_last_error": (ctypes.c_char_p, [ctypes.c_void_p]),
     "agatha_version": (ctypes.c_int32, []),
+    "agatha_tune_variants": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(agatha_params),
+                                            ctypes.c_int32, ctypes.POINTER(ctypes.c_int32)]),
 }
 
 
@@ -224,9 +232,11 @@ class Context:
     """An ``agatha_ctx`` on one device."""
 
     def __init__(self, device: int = 0, mem_budget_bytes: int = 0, max_pairs: int = 0,
-                 tune_cache_path: Optional[str] = None, timing: bool = False):
+                 tune_cache_path: Optional[str] = None, timing: bool = False,
+                 autotune: bool = False):
         self._ptr = ctypes.c_void_p()
-        cfg = agatha_config(device, AGATHA_CFG_TIMING if timing else 0, mem_budget_bytes, max_pairs,
+        flags = (AGATHA_CFG_TIMING if timing else 0) | (AGATHA_CFG_AUTOTUNE if autotune else 0)
+        cfg = agatha_config(device, flags, mem_budget_bytes, max_pairs,
                             tune_cache_path.encode() if tune_cache_path else None)
         _check(lib().agatha_init(ctypes.byref(self._ptr), ctypes.byref(cfg)), what="agatha_init")
 
@@ -259,6 +269,19 @@ class Context:
 
     def last_error(self) -> str:
         return lib().agatha_last_error(self._ptr).decode()
+
+    def tune_variants(self, scoring, w_max: Optional[int] = None):
+        """The autotuner's variant per length class (indices into
+        VARIANT_NAMES) followed by the split flag, or None if these parameters
+        were not tuned yet."""
+        v = (ctypes.c_int32 * 5)()
+        p = make_params(scoring)
+        rc = lib().agatha_tune_variants(self._ptr, ctypes.byref(p),
+                                        ctypes.c_int32(scoring.w if w_max is None else w_max), v)
+        if rc == AGATHA_EAGAIN:
+            return None
+        _check(rc, self._ptr, "agatha_tune_variants")
+        return [int(x) for x in v]
 
     # -- alignment ---------------------------------------------------------
     def align_host(self, pb: PackedBatch, scoring, flags: int = 0, stream: int = 0,

@@ -45,9 +45,7 @@ struct DevBatch {
     int64_t n_pairs;
     // schedule produced by the prep kernels
     int32_t *order;          // pair indices, longest predicted work first
-    int32_t *counters;       // [0] queue head of the batched kernel, [1] count of
-                             // pairs routed to the batched kernel, [2] wide pairs,
-                             // [3] error word
+    int32_t *counters;       // queue heads and counts (CTR_*), [3] error word
     int32_t *wide_order;     // pairs whose band is too wide for the warp kernel
     int64_t *bucket_hist;    // scratch for the ordering
     int32_t *ovf_list;       // pairs the 16-bit kernel hands back to the 32-bit one
@@ -57,10 +55,30 @@ struct DevBatch {
 };
 
 enum : int32_t { CTR_HEAD = 0, CTR_NWARP = 1, CTR_NWIDE = 2, CTR_ERR = 3, CTR_WIDE_HEAD = 4,
-                 CTR_NOVF = 5, CTR_OVF_HEAD = 6, CTR_COUNT = 8 };
+                 CTR_NOVF = 5, CTR_OVF_HEAD = 6, CTR_CLS_HEAD = 8, CTR_COUNT = 12 };
 
-// Which pair list a warp kernel launch walks.
-enum : int32_t { WARP_LIST_MAIN = 0, WARP_LIST_OVERFLOW = 1 };
+// Which pair list a warp kernel launch walks: the whole ordered queue, the
+// pairs the 16-bit kernel handed back, or the part of the ordered queue that
+// holds one length class (WARP_LIST_CLASS + c).
+enum : int32_t { WARP_LIST_MAIN = 0, WARP_LIST_OVERFLOW = 1, WARP_LIST_CLASS = 2 };
+
+// Length classes the kernel choice is tuned for, by predicted band cells:
+// class 0 >= 2^25, class 1 >= 2^23, class 2 >= 2^21, class 3 the rest.  In
+// the ordering's buckets (bucket = 255 - (4 floor(log2 cells) + quarter)),
+// class c holds buckets [CLASS_BUCKET[c], CLASS_BUCKET[c + 1]).
+constexpr int N_CLASSES = 4;
+__host__ __device__ inline int32_t class_first_bucket(int c) {
+    return c <= 0 ? 0 : (c == 1 ? 156 : (c == 2 ? 164 : (c == 3 ? 172 : 256)));
+}
+__host__ __device__ inline int32_t class_of_cells(uint64_t est) {
+    int32_t lg = 0;
+    while ((est >> lg) > 1) ++lg;                     // floor(log2), est >= 1
+    return lg >= 25 ? 0 : (lg >= 23 ? 1 : (lg >= 21 ? 2 : 3));
+}
+// Predicted band cells of a pair (Section 4.5 model): anti-diagonals x band.
+__host__ __device__ inline uint64_t predicted_cells(int32_t tlen, int32_t qlen, int32_t w) {
+    return (uint64_t)(tlen + qlen) * (uint64_t)(w + 1) / 2 + 1;
+}
 
 // device error codes written to counters[CTR_ERR]
 enum : int32_t { DEV_ERR_NONE = 0, DEV_ERR_BAD_PAIR = 1 };
@@ -153,6 +171,38 @@ __device__ __forceinline__ bool pair_valid(const DevBatch &B, int64_t i) {
     return true;
 }
 
+// The pairs one warp-kernel launch walks: items[begin..end) (input order
+// when items is null), handed out through the queue head *head.
+struct WorkList {
+    const int32_t *items;
+    int32_t *head;
+    int32_t begin, end;
+};
+
+__device__ __forceinline__ WorkList work_list(const DevBatch &B, int32_t list) {
+    WorkList L;
+    if (list == WARP_LIST_OVERFLOW) {
+        L.items = B.ovf_list;
+        L.head = &B.counters[CTR_OVF_HEAD];
+        L.begin = 0;
+        L.end = B.counters[CTR_NOVF];
+    } else if (list >= WARP_LIST_CLASS) {
+        // after the ordering, bucket_hist[b] is the end of bucket b in `order`
+        const int c = list - WARP_LIST_CLASS;
+        const int32_t b0 = class_first_bucket(c), b1 = class_first_bucket(c + 1);
+        L.items = B.order;
+        L.head = &B.counters[CTR_CLS_HEAD + c];
+        L.begin = b0 > 0 ? (int32_t)B.bucket_hist[b0 - 1] : 0;
+        L.end = (int32_t)B.bucket_hist[b1 - 1];
+    } else {
+        L.items = B.order;
+        L.head = &B.counters[CTR_HEAD];
+        L.begin = 0;
+        L.end = B.order ? B.counters[CTR_NWARP] : (int32_t)B.n_pairs;
+    }
+    return L;
+}
+
 // Launchers (defined in the .cu files).
 cudaError_t launch_prep(const DevBatch *d_batch, int64_t n_pairs, int32_t sort, cudaStream_t s,
                         int n_sm);
@@ -161,9 +211,11 @@ cudaError_t launch_warp_c(const DevBatch *d_batch, int n_blocks, cudaStream_t s,
                           int list = WARP_LIST_MAIN);
 template <int C>
 int occupancy_warp_c();
-template <int C>
-cudaError_t launch_warp16_c(const DevBatch *d_batch, int n_blocks, cudaStream_t s, int use_fast);
-template <int C>
+// MINB: resident blocks per SM the 16-bit kernel's registers are cut for.
+template <int C, int MINB>
+cudaError_t launch_warp16_c(const DevBatch *d_batch, int n_blocks, cudaStream_t s, int use_fast,
+                            int list = WARP_LIST_MAIN);
+template <int C, int MINB>
 int occupancy_warp16_c();
 cudaError_t launch_plain_kernel(const DevBatch *d_batch, int64_t n_blocks, int32_t w_max,
                                 int use_wide_list, cudaStream_t s);

@@ -18,7 +18,7 @@ constexpr int N_BUCKETS = 256;
 
 // Bucket 0 holds the largest predicted work.
 __device__ __forceinline__ int32_t work_bucket(int32_t tlen, int32_t qlen, int32_t w) {
-    const uint64_t est = (uint64_t)(tlen + qlen) * (uint64_t)(w + 1) / 2 + 1;
+    const uint64_t est = predicted_cells(tlen, qlen, w);
     const int32_t lg = 63 - __clzll(est);                    // floor(log2)
     const int32_t frac = lg >= 2 ? (int32_t)((est >> (lg - 2)) & 3) : 0;
     int32_t key = lg * 4 + frac;                              // 4 buckets per octave

@@ -330,19 +330,14 @@ __global__ void __launch_bounds__(WARP_BLOCK_THREADS)
 warp_align_kernel(const DevBatch *__restrict__ d_batch, int32_t use_fast, int32_t list) {
     const DevBatch B = *d_batch;
     const int lane = threadIdx.x & 31;
-    const bool ovf = list == WARP_LIST_OVERFLOW;
-    const bool sorted = ovf || B.order != nullptr;
-    const int32_t *items = ovf ? B.ovf_list : B.order;
-    int32_t *head = &B.counters[ovf ? CTR_OVF_HEAD : CTR_HEAD];
-    const int64_t n_work = ovf ? (int64_t)B.counters[CTR_NOVF]
-                               : (sorted ? (int64_t)B.counters[CTR_NWARP] : B.n_pairs);
+    const WorkList L = work_list(B, list);
     for (;;) {
         int32_t k = 0;
-        if (lane == 0) k = atomicAdd(head, 1);
+        if (lane == 0) k = L.begin + atomicAdd(L.head, 1);
         k = __shfl_sync(FULL, k, 0);
-        if (k >= n_work) break;
-        const int32_t pair = sorted ? items[k] : k;
-        if (!sorted && (!pair_valid(B, pair) || !warp_takes(B, pair))) continue;
+        if (k >= L.end) break;
+        const int32_t pair = L.items ? L.items[k] : k;
+        if (!L.items && (!pair_valid(B, pair) || !warp_takes(B, pair))) continue;
         WarpPair<C> wp;
         wp.run(B, pair, lane, use_fast != 0);
     }

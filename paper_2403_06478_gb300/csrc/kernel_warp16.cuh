@@ -571,26 +571,20 @@ struct WarpPair16 {
     }
 };
 
-// Resident blocks per SM the register budget is cut for: 4 blocks (128
-// registers a thread) up to 16 slots per lane, 3 (168) for 24.
-template <int C>
-constexpr int warp16_min_blocks() { return C <= 16 ? 4 : 3; }
-
-template <int C>
-__global__ void __launch_bounds__(WARP_BLOCK_THREADS, warp16_min_blocks<C>())
-warp16_align_kernel(const DevBatch *__restrict__ d_batch, int32_t use_fast) {
+template <int C, int MINB>
+__global__ void __launch_bounds__(WARP_BLOCK_THREADS, MINB)
+warp16_align_kernel(const DevBatch *__restrict__ d_batch, int32_t use_fast, int32_t list) {
     __shared__ Cold16 cold[WARP_BLOCK_THREADS / 32];
     const DevBatch B = *d_batch;
     const int lane = threadIdx.x & 31;
-    const bool sorted = B.order != nullptr;
-    const int64_t n_work = sorted ? (int64_t)B.counters[CTR_NWARP] : B.n_pairs;
+    const WorkList L = work_list(B, list);
     for (;;) {
         int32_t k = 0;
-        if (lane == 0) k = atomicAdd(&B.counters[CTR_HEAD], 1);
+        if (lane == 0) k = L.begin + atomicAdd(L.head, 1);
         k = __shfl_sync(FULL, k, 0);
-        if (k >= n_work) break;
-        const int32_t pair = sorted ? B.order[k] : k;
-        if (!sorted && (!pair_valid(B, pair) || !warp_takes(B, pair))) continue;
+        if (k >= L.end) break;
+        const int32_t pair = L.items ? L.items[k] : k;
+        if (!L.items && (!pair_valid(B, pair) || !warp_takes(B, pair))) continue;
         WarpPair16<C> wp(cold[threadIdx.x >> 5]);
         if (!wp.run(B, pair, lane, use_fast != 0) && lane == 0) {
             const int32_t slot = atomicAdd(&B.counters[CTR_NOVF], 1);
@@ -599,16 +593,17 @@ warp16_align_kernel(const DevBatch *__restrict__ d_batch, int32_t use_fast) {
     }
 }
 
-template <int C>
-cudaError_t launch_warp16_c(const DevBatch *d_batch, int n_blocks, cudaStream_t s, int use_fast) {
-    warp16_align_kernel<C><<<n_blocks, WARP_BLOCK_THREADS, 0, s>>>(d_batch, use_fast);
+template <int C, int MINB>
+cudaError_t launch_warp16_c(const DevBatch *d_batch, int n_blocks, cudaStream_t s, int use_fast,
+                            int list) {
+    warp16_align_kernel<C, MINB><<<n_blocks, WARP_BLOCK_THREADS, 0, s>>>(d_batch, use_fast, list);
     return cudaGetLastError();
 }
 
-template <int C>
+template <int C, int MINB>
 int occupancy_warp16_c() {
     int nb = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, warp16_align_kernel<C>,
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, warp16_align_kernel<C, MINB>,
                                                       WARP_BLOCK_THREADS, 0) != cudaSuccess)
         return 1;
     return nb > 0 ? nb : 1;

@@ -1,8 +1,11 @@
-// Instantiation of the 16-bit packed-lane warp kernel for 16 band slots per
-// lane (w <= 511).
+// Instantiations of the 16-bit packed-lane warp kernel for 16 band slots per
+// lane (w <= 511), at two register budgets (resident blocks per SM): the
+// autotuner picks one per length class.
 #include "kernel_warp16.cuh"
 
 namespace agatha {
-template cudaError_t launch_warp16_c<16>(const DevBatch *, int, cudaStream_t, int);
-template int occupancy_warp16_c<16>();
+template cudaError_t launch_warp16_c<16, 4>(const DevBatch *, int, cudaStream_t, int, int);
+template int occupancy_warp16_c<16, 4>();
+template cudaError_t launch_warp16_c<16, 3>(const DevBatch *, int, cudaStream_t, int, int);
+template int occupancy_warp16_c<16, 3>();
 }  // namespace agatha

@@ -162,19 +162,28 @@ static cudaError_t launch_warp(int C, const DevBatch *d, int blocks, cudaStream_
     }
 }
 
-static cudaError_t launch_warp16(int C, const DevBatch *d, int blocks, cudaStream_t s, int fast) {
-    switch (C) {
-        case 8: return launch_warp16_c<8>(d, blocks, s, fast);
-        case 16: return launch_warp16_c<16>(d, blocks, s, fast);
-        default: return launch_warp16_c<24>(d, blocks, s, fast);
+// 16-bit kernel with C slots per lane; high: the larger register budget
+// (one resident block per SM fewer).
+static cudaError_t launch_warp16(int C, int high, const DevBatch *d, int blocks, cudaStream_t s,
+                                 int fast, int list) {
+    switch (C * 2 + high) {
+        case 16: return launch_warp16_c<8, 4>(d, blocks, s, fast, list);
+        case 17: return launch_warp16_c<8, 3>(d, blocks, s, fast, list);
+        case 32: return launch_warp16_c<16, 4>(d, blocks, s, fast, list);
+        case 33: return launch_warp16_c<16, 3>(d, blocks, s, fast, list);
+        case 48: return launch_warp16_c<24, 3>(d, blocks, s, fast, list);
+        default: return launch_warp16_c<24, 2>(d, blocks, s, fast, list);
     }
 }
 
-int warp16_occupancy(int C) {
-    switch (C) {
-        case 8: return occupancy_warp16_c<8>();
-        case 16: return occupancy_warp16_c<16>();
-        default: return occupancy_warp16_c<24>();
+int warp16_occupancy(int C, int high) {
+    switch (C * 2 + high) {
+        case 16: return occupancy_warp16_c<8, 4>();
+        case 17: return occupancy_warp16_c<8, 3>();
+        case 32: return occupancy_warp16_c<16, 4>();
+        case 33: return occupancy_warp16_c<16, 3>();
+        case 48: return occupancy_warp16_c<24, 3>();
+        default: return occupancy_warp16_c<24, 2>();
     }
 }
 
@@ -218,15 +227,39 @@ static cudaError_t enqueue_part(agatha_ctx *ctx, Slot *sl, const LaunchPlan &lp,
         return launch_prep(d, lp.n, lp.plain ? 0 : lp.sort, s, ctx->n_sm);
     }
     if (lp.plain) return launch_plain_kernel(d, lp.plain_blocks, lp.plain_w, 0, s);
-    if (lp.lane16) {
-        e = launch_warp16(lp.C16, d, lp.warp16_blocks, s, lp.fast);
+    bool any16 = false;
+    if (!lp.split) {
+        if (lp.lane16) {
+            e = launch_warp16(lp.C16, lp.regs_high, d, lp.warp16_blocks[lp.regs_high], s, lp.fast,
+                              WARP_LIST_MAIN);
+            any16 = true;
+        } else {
+            e = launch_warp(lp.C, d, lp.warp_blocks, s, lp.fast, WARP_LIST_MAIN);
+        }
         if (e != cudaSuccess) return e;
-        // pairs whose scores left the 16-bit range, recomputed on int32 lanes
-        e = launch_warp(lp.C, d, lp.warp_blocks, s, lp.fast, WARP_LIST_OVERFLOW);
     } else {
-        e = launch_warp(lp.C, d, lp.warp_blocks, s, lp.fast, WARP_LIST_MAIN);
+        // one launch per length class, each on its own branch so that the next
+        // class's blocks take SMs as the longer class's blocks drain
+        if ((e = cudaEventRecord(sl->fork, s)) != cudaSuccess) return e;
+        for (int c = 0; c < N_CLASSES; ++c) {
+            cudaStream_t sc = sl->aux[c];
+            if ((e = cudaStreamWaitEvent(sc, sl->fork, 0)) != cudaSuccess) return e;
+            const int v = lp.cls_var[c];
+            if (v == VAR_32) {
+                e = launch_warp(lp.C, d, lp.warp_blocks, sc, lp.fast, WARP_LIST_CLASS + c);
+            } else {
+                e = launch_warp16(lp.C16, v == VAR_16_HIGHREG, d, lp.warp16_blocks[v == VAR_16_HIGHREG],
+                                  sc, lp.fast, WARP_LIST_CLASS + c);
+                any16 = true;
+            }
+            if (e != cudaSuccess) return e;
+            if ((e = cudaEventRecord(sl->join[c], sc)) != cudaSuccess) return e;
+            if ((e = cudaStreamWaitEvent(s, sl->join[c], 0)) != cudaSuccess) return e;
+        }
     }
-    if (e != cudaSuccess) return e;
+    // pairs whose scores left the 16-bit range, recomputed on int32 lanes
+    if (any16 && (e = launch_warp(lp.C, d, lp.warp_blocks, s, lp.fast, WARP_LIST_OVERFLOW)) != cudaSuccess)
+        return e;
     if (lp.wide_w > 0) e = launch_plain_kernel(d, (int64_t)ctx->n_sm * 2, lp.wide_w, 1, s);
     return e;
 }
@@ -270,6 +303,16 @@ int slot_init(agatha_ctx *ctx, Ledger &ledger, Slot *sl) {
         (rc = sl->desc.ensure(ctx, ledger, sizeof(DevBatch))))
         return rc;
     sl->d_desc = (DevBatch *)sl->desc.ptr;
+    for (int c = 0; c < N_CLASSES; ++c)
+        if (cudaStreamCreateWithFlags(&sl->aux[c], cudaStreamNonBlocking) != cudaSuccess ||
+            cudaEventCreateWithFlags(&sl->join[c], cudaEventDisableTiming) != cudaSuccess) {
+            cudaGetLastError();
+            return set_error(ctx, AGATHA_ECUDA, "slot streams");
+        }
+    if (cudaEventCreateWithFlags(&sl->fork, cudaEventDisableTiming) != cudaSuccess) {
+        cudaGetLastError();
+        return set_error(ctx, AGATHA_ECUDA, "slot events");
+    }
     if (cudaMallocHost(&sl->h_desc, sizeof(DevBatch)) != cudaSuccess ||
         cudaMallocHost(&sl->h_counters, CTR_COUNT * sizeof(int32_t)) != cudaSuccess) {
         cudaGetLastError();
@@ -287,6 +330,14 @@ void slot_release(Ledger &ledger, Slot *sl) {
     for (DevBuf *b : bufs) b->release(ledger);
     if (sl->h_desc) cudaFreeHost(sl->h_desc);
     if (sl->h_counters) cudaFreeHost(sl->h_counters);
+    for (int c = 0; c < N_CLASSES; ++c) {
+        if (sl->aux[c]) cudaStreamDestroy(sl->aux[c]);
+        if (sl->join[c]) cudaEventDestroy(sl->join[c]);
+        sl->aux[c] = nullptr;
+        sl->join[c] = nullptr;
+    }
+    if (sl->fork) cudaEventDestroy(sl->fork);
+    sl->fork = nullptr;
     sl->h_desc = nullptr;
     sl->h_counters = nullptr;
     sl->d_desc = nullptr;
@@ -351,9 +402,12 @@ int make_plan(agatha_ctx *ctx, const DevParams &p, const BatchShape &shape, uint
     // score by at most 64 (the headroom the 16-bit kernel's rebasing keeps)
     lp->C16 = pick_slots16(shape.max_w_all);
     lp->lane16 = !(flags & AGATHA_FORCE32) && lp->C16 > 0 && step_change_max(p) <= 64 && !lp->wide_w;
+    lp->regs_high = (flags & AGATHA_REGS_HIGH) ? 1 : 0;
+    lp->split = 0;
     if (lp->lane16) {
         lp->warp_w_max = 32 * lp->C16 - 1;
-        lp->warp16_blocks = ctx->n_sm * warp16_occupancy(lp->C16);
+        lp->warp16_blocks[0] = ctx->n_sm * warp16_occupancy(lp->C16, 0);
+        lp->warp16_blocks[1] = ctx->n_sm * warp16_occupancy(lp->C16, 1);
     }
     lp->plain_w = 0;
     lp->plain_blocks = 0;
@@ -418,6 +472,8 @@ extern "C" int agatha_init(agatha_ctx **out, const agatha_config *cfg) {
         agatha_destroy(ctx);
         return rc;
     }
+    ctx->autotune = (c.flags & AGATHA_CFG_AUTOTUNE) != 0;
+    tune_load(ctx);
     if (c.flags & AGATHA_CFG_TIMING) {
         ctx->timing = true;
         if (cudaEventCreate(&ctx->ev_k0) != cudaSuccess || cudaEventCreate(&ctx->ev_k1) != cudaSuccess) {
@@ -441,6 +497,8 @@ extern "C" void agatha_destroy(agatha_ctx *ctx) {
     cudaSetDevice(ctx->device);
     if (ctx->stream) cudaStreamSynchronize(ctx->stream);
     slot_release(ctx->ledger, &ctx->main);
+    if (ctx->tune_ev0) cudaEventDestroy(ctx->tune_ev0);
+    if (ctx->tune_ev1) cudaEventDestroy(ctx->tune_ev1);
     if (ctx->ev_k0) cudaEventDestroy(ctx->ev_k0);
     if (ctx->ev_k1) cudaEventDestroy(ctx->ev_k1);
     if (ctx->stream) cudaStreamDestroy(ctx->stream);
@@ -454,43 +512,15 @@ extern "C" const char *agatha_last_error(agatha_ctx *ctx) {
     return ctx->last_error_copy.c_str();
 }
 
-extern "C" int agatha_align_batch(agatha_ctx *ctx, const agatha_batch *batch,
-                                  const agatha_params *params, agatha_result *out, uint32_t flags,
-                                  void *stream) {
-    if (!ctx || !batch || !params) return AGATHA_EINVAL;
-    std::lock_guard<std::mutex> lock(ctx->mu);
-    DevParams p;
-    if (normalise_params(params, &p)) return set_error(ctx, AGATHA_EINVAL, "bad scoring parameters");
-    if (batch->n_pairs < 0) return set_error(ctx, AGATHA_EINVAL, "negative n_pairs");
-    if (batch->n_pairs > 0 && !out) return set_error(ctx, AGATHA_EINVAL, "null out");
-    const bool dev = (flags & AGATHA_DEVICE_PTRS) != 0;
-    if ((flags & AGATHA_ASYNC) && !dev) return set_error(ctx, AGATHA_EINVAL, "ASYNC needs DEVICE_PTRS");
-    cudaError_t e = cudaSetDevice(ctx->device);
-    if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaSetDevice");
-    cudaStream_t s = stream ? (cudaStream_t)stream : ctx->stream;
-    const int64_t n = batch->n_pairs;
-    if (n == 0) return AGATHA_OK;
+namespace agatha {
 
-    BatchShape shape;
-    if (!dev) {
-        int rc = validate_host_batch(ctx, batch, p, &shape);
-        if (rc) return rc;
-    } else {
-        shape.n = n;
-        shape.max_len = 0;
-        // lengths live on the device: plan for the widest band the parameters allow
-        shape.max_w_all = p.w >= 0 ? p.w : 32 * 32 - 1;
-        shape.max_w_warp = shape.max_w_all;
-        if (batch->q_words < 0 || batch->t_words < 0)
-            return set_error(ctx, AGATHA_EINVAL, "negative stream size");
-    }
-    LaunchPlan lp;
-    int rc = make_plan(ctx, p, shape, flags, &lp);
-    if (rc) return rc;
-    if (dev && p.w < 0 && !lp.plain) {
-        // unbanded device batch: pairs wider than the warp kernel go to the block kernel
-        lp.wide_w = plain_kernel_max_w();
-    }
+// Stage one batch on the context's slot and run it with plan lp (ctx->mu held).
+int run_planned(agatha_ctx *ctx, const agatha_batch *batch, const DevParams &p, agatha_result *out,
+                uint32_t flags, cudaStream_t s, const LaunchPlan &lp, cudaEvent_t ev0, cudaEvent_t ev1) {
+    const bool dev = (flags & AGATHA_DEVICE_PTRS) != 0;
+    const int64_t n = batch->n_pairs;
+    cudaError_t e;
+    int rc;
     Slot *sl = &ctx->main;
     if ((rc = slot_ensure(ctx, ctx->ledger, sl, n, batch->q_words, batch->t_words, !dev))) return rc;
 
@@ -533,10 +563,7 @@ extern "C" int agatha_align_batch(agatha_ctx *ctx, const agatha_batch *batch,
     if ((e = cudaMemcpyAsync(sl->d_desc, d, sizeof(DevBatch), cudaMemcpyHostToDevice, s)) != cudaSuccess)
         return cuda_fail(ctx, e, "copy descriptor");
     sl->last_stream = s;
-    if ((e = slot_run(ctx, sl, lp, s, ctx->timing ? ctx->ev_k0 : nullptr, ctx->timing ? ctx->ev_k1 : nullptr)) !=
-        cudaSuccess)
-        return cuda_fail(ctx, e, "launch");
-    ctx->timed_once = true;
+    if ((e = slot_run(ctx, sl, lp, s, ev0, ev1)) != cudaSuccess) return cuda_fail(ctx, e, "launch");
     if ((e = cudaMemcpyAsync(sl->h_counters, sl->counters.ptr, CTR_COUNT * sizeof(int32_t),
                              cudaMemcpyDeviceToHost, s)) != cudaSuccess)
         return cuda_fail(ctx, e, "copy counters");
@@ -550,6 +577,52 @@ extern "C" int agatha_align_batch(agatha_ctx *ctx, const agatha_batch *batch,
     if (sl->h_counters[CTR_ERR] != DEV_ERR_NONE)
         return set_error(ctx, AGATHA_EINVAL, "a pair has a bad length, offset or score range");
     return AGATHA_OK;
+}
+
+}  // namespace agatha
+
+extern "C" int agatha_align_batch(agatha_ctx *ctx, const agatha_batch *batch,
+                                  const agatha_params *params, agatha_result *out, uint32_t flags,
+                                  void *stream) {
+    if (!ctx || !batch || !params) return AGATHA_EINVAL;
+    std::lock_guard<std::mutex> lock(ctx->mu);
+    DevParams p;
+    if (normalise_params(params, &p)) return set_error(ctx, AGATHA_EINVAL, "bad scoring parameters");
+    if (batch->n_pairs < 0) return set_error(ctx, AGATHA_EINVAL, "negative n_pairs");
+    if (batch->n_pairs > 0 && !out) return set_error(ctx, AGATHA_EINVAL, "null out");
+    const bool dev = (flags & AGATHA_DEVICE_PTRS) != 0;
+    if ((flags & AGATHA_ASYNC) && !dev) return set_error(ctx, AGATHA_EINVAL, "ASYNC needs DEVICE_PTRS");
+    cudaError_t e = cudaSetDevice(ctx->device);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaSetDevice");
+    cudaStream_t s = stream ? (cudaStream_t)stream : ctx->stream;
+    const int64_t n = batch->n_pairs;
+    if (n == 0) return AGATHA_OK;
+
+    BatchShape shape;
+    if (!dev) {
+        int rc = validate_host_batch(ctx, batch, p, &shape);
+        if (rc) return rc;
+    } else {
+        shape.n = n;
+        shape.max_len = 0;
+        // lengths live on the device: plan for the widest band the parameters allow
+        shape.max_w_all = p.w >= 0 ? p.w : 32 * 32 - 1;
+        shape.max_w_warp = shape.max_w_all;
+        if (batch->q_words < 0 || batch->t_words < 0)
+            return set_error(ctx, AGATHA_EINVAL, "negative stream size");
+    }
+    LaunchPlan lp;
+    int rc = make_plan(ctx, p, shape, flags, &lp);
+    if (rc) return rc;
+    if (dev && p.w < 0 && !lp.plain) {
+        // unbanded device batch: pairs wider than the warp kernel go to the block kernel
+        lp.wide_w = plain_kernel_max_w();
+    }
+    if ((rc = tune_apply(ctx, batch, p, flags, s, &lp))) return rc;
+    rc = run_planned(ctx, batch, p, out, flags, s, lp, ctx->timing ? ctx->ev_k0 : nullptr,
+                     ctx->timing ? ctx->ev_k1 : nullptr);
+    if (rc == AGATHA_OK) ctx->timed_once = true;
+    return rc;
 }
 
 extern "C" int agatha_last_kernel_ms(agatha_ctx *ctx, float *ms) {

@@ -1,6 +1,7 @@
 // Host-side internals of the library (not part of the C ABI).
 #pragma once
 
+#include <array>
 #include <condition_variable>
 #include <cstdint>
 #include <deque>
@@ -42,20 +43,35 @@ struct BatchShape {
     int32_t max_w_warp = 0;
 };
 
-using PlanKey = std::tuple<int, int, int, int, int32_t, int, int>;
+using PlanKey = std::array<int32_t, 12>;
+
+// Kernel variant of a length class.
+enum : int8_t { VAR_16 = 0, VAR_16_HIGHREG = 1, VAR_32 = 2, N_VARIANTS = 3 };
+
+// What the autotuner keeps per key: the variant of each length class and
+// whether one launch per class beat a single launch.
+struct TuneChoice {
+    int8_t var[N_CLASSES] = {VAR_16, VAR_16, VAR_16, VAR_16};
+    int8_t split = 0;
+};
 
 struct LaunchPlan {
     int64_t n = 0;
     int plain = 0, sort = 1, fast = 1, use_graph = 1;
-    int C = 16;
+    int C = 16;                 // slots per lane of the int32 kernel
     int32_t warp_w_max = 0;
     int warp_blocks = 0;
-    int lane16 = 0, C16 = 0, warp16_blocks = 0, minb16 = 4;
+    int lane16 = 0, C16 = 0;    // 16-bit lanes allowed; their slots per lane
+    int regs_high = 0;          // 16-bit kernel at its larger register budget
+    int warp16_blocks[2] = {0, 0};   // grid of the 16-bit kernel per budget
+    int split = 0;              // one launch per length class, variant cls_var[c]
+    int8_t cls_var[N_CLASSES] = {VAR_16, VAR_16, VAR_16, VAR_16};
     int32_t wide_w = 0;         // > 0: pairs wider than the warp kernel exist
     int32_t plain_w = 0;
     int64_t plain_blocks = 0;
     PlanKey key() const {
-        return std::make_tuple(plain, C + 100 * C16 * lane16, sort, fast, wide_w, warp_blocks, minb16);
+        return {plain, C, C16 * lane16, regs_high, sort, fast, wide_w, warp_blocks, split,
+                split ? cls_var[0] | (cls_var[1] << 4) | (cls_var[2] << 8) | (cls_var[3] << 12) : 0, 0, 0};
     }
 };
 
@@ -67,6 +83,8 @@ struct Slot {
         counters, hist, desc;
     DevBatch *d_desc = nullptr;
     DevBatch *h_desc = nullptr;       // pinned staging of the descriptor
+    cudaStream_t aux[N_CLASSES] = {}; // branches of the per-class launches
+    cudaEvent_t fork = nullptr, join[N_CLASSES] = {};
     int32_t *h_counters = nullptr;    // pinned copy of the counters after a batch
     cudaStream_t last_stream = nullptr;
     std::map<std::tuple<int, PlanKey>, cudaGraphExec_t> graphs;
@@ -79,7 +97,7 @@ int validate_host_batch(agatha_ctx *ctx, const agatha_batch *b, const DevParams 
 int pick_slots_per_lane(int32_t w);
 int pick_slots16(int32_t w);
 int warp_occupancy(int C);
-int warp16_occupancy(int C);
+int warp16_occupancy(int C, int high);
 
 int slot_init(agatha_ctx *ctx, Ledger &ledger, Slot *s);
 void slot_release(Ledger &ledger, Slot *s);
@@ -98,6 +116,18 @@ cudaError_t slot_run(agatha_ctx *ctx, Slot *s, const LaunchPlan &lp, cudaStream_
 // Stop and free the context's server, if any (serve.cu).
 void serve_free(agatha_ctx *ctx);
 
+// Stage one batch on the context's own slot and run it with plan lp; ev0/ev1
+// (may be null) bracket the alignment kernels.  ctx->mu must be held.
+int run_planned(agatha_ctx *ctx, const agatha_batch *batch, const DevParams &p, agatha_result *out,
+                uint32_t flags, cudaStream_t s, const LaunchPlan &lp, cudaEvent_t ev0, cudaEvent_t ev1);
+
+// Autotuner (tune.cu): read the cache file; turn lp into per-class launches
+// with the tuned variants, measuring them first if this key is new and the
+// batch is on the host.
+void tune_load(agatha_ctx *ctx);
+int tune_apply(agatha_ctx *ctx, const agatha_batch *batch, const DevParams &p, uint32_t flags,
+               cudaStream_t s, LaunchPlan *lp);
+
 }  // namespace agatha
 
 struct agatha_ctx {
@@ -115,4 +145,7 @@ struct agatha_ctx {
     bool timing = false;               // AGATHA_CFG_TIMING
     bool timed_once = false;
     cudaEvent_t ev_k0 = nullptr, ev_k1 = nullptr;
+    bool autotune = false;             // AGATHA_CFG_AUTOTUNE
+    std::map<std::string, agatha::TuneChoice> tune_table;
+    cudaEvent_t tune_ev0 = nullptr, tune_ev1 = nullptr;
 };

@@ -1,0 +1,221 @@
+// Autotuner: which kernel variant runs each length class of the ordered queue.
+//
+// The paper picks its slice width and subwarp size by sweeping them on its
+// datasets (Sections 5.5 and 5.7).  Here the knobs are those of the warp
+// kernels: 16-bit packed lanes or int32 lanes, and the register budget of
+// the 16-bit kernel (fewer resident warps, more registers each).  They are
+// chosen per length class, by measurement, the first time a host batch
+// arrives for a scoring and band width: the pairs of each class (up to 4096,
+// spread over the class) are aligned with every variant and the fastest one
+// kept (a variant other than the default must win by 3%).  One launch per
+// class adds the tail of each launch, so the split is kept only if the batch
+// itself (up to 32768 of its pairs) runs at least 3% faster split than as
+// one launch.
+// Every variant computes the same exact results, so the choice only moves
+// time.  Choices are kept per context and, with a cache path, in a text file
+// (one line per key: the key, the four class variants and the split flag).
+#include <algorithm>
+#include <cstdio>
+#include <fstream>
+#include <sstream>
+#include <string>
+#include <vector>
+
+#include "runtime.h"
+
+namespace agatha {
+
+namespace {
+
+constexpr int64_t kTuneMaxPairs = 4096;       // per class, to pick its variant
+constexpr int64_t kTuneSplitPairs = 32768;    // of the whole batch, to decide the split
+
+std::string tune_key(const agatha_ctx *ctx, const DevParams &p, int C16) {
+    char buf[256];
+    std::snprintf(buf, sizeof(buf), "sm%d_cc%d%d_a%d_b%d_q%d_e%d_q2%d_e2%d_w%d_z%d_c%d", ctx->n_sm,
+                  ctx->cc_major, ctx->cc_minor, p.a, p.b, p.q, p.e, p.q2, p.e2, p.w, p.zdrop, C16);
+    return buf;
+}
+
+void tune_save(agatha_ctx *ctx) {
+    if (ctx->tune_cache_path.empty()) return;
+    const std::string tmp = ctx->tune_cache_path + ".tmp";
+    {
+        std::ofstream f(tmp, std::ios::trunc);
+        if (!f) return;
+        for (const auto &kv : ctx->tune_table) {
+            f << kv.first;
+            for (int8_t v : kv.second.var) f << ' ' << (int)v;
+            f << ' ' << (int)kv.second.split << '\n';
+        }
+    }
+    std::rename(tmp.c_str(), ctx->tune_cache_path.c_str());
+}
+
+// Median kernel time of three runs of a sub-batch under plan vp (after one
+// untimed run).
+int time_plan(agatha_ctx *ctx, const agatha_batch &sb, const DevParams &p, uint32_t flags,
+              cudaStream_t s, LaunchPlan vp, std::vector<agatha_result> &res, float *ms) {
+    vp.n = sb.n_pairs;
+    vp.use_graph = 0;
+    const uint32_t f = flags & ~(uint32_t)(AGATHA_DEVICE_PTRS | AGATHA_ASYNC);
+    int rc = run_planned(ctx, &sb, p, res.data(), f, s, vp, nullptr, nullptr);
+    if (rc) return rc;
+    float t[3];
+    for (float &x : t) {
+        rc = run_planned(ctx, &sb, p, res.data(), f, s, vp, ctx->tune_ev0, ctx->tune_ev1);
+        if (rc) return rc;
+        const cudaError_t e = cudaEventElapsedTime(&x, ctx->tune_ev0, ctx->tune_ev1);
+        if (e != cudaSuccess) return cuda_fail(ctx, e, "tuning timer");
+    }
+    std::sort(t, t + 3);
+    *ms = t[1];
+    return AGATHA_OK;
+}
+
+LaunchPlan single_variant(LaunchPlan vp, int variant) {
+    vp.split = 0;
+    vp.lane16 = variant != VAR_32;
+    vp.regs_high = variant == VAR_16_HIGHREG;
+    return vp;
+}
+
+// A sub-batch of at most `cap` of the given pairs, spread over them.
+struct SubBatch {
+    std::vector<int64_t> qo, to;
+    std::vector<int32_t> ql, tl;
+    agatha_batch b;
+    SubBatch(const agatha_batch *src, const std::vector<int64_t> &m, int64_t cap) {
+        const int64_t k = std::min<int64_t>((int64_t)m.size(), cap);
+        qo.resize(k); to.resize(k); ql.resize(k); tl.resize(k);
+        for (int64_t j = 0; j < k; ++j) {
+            const int64_t i = m[(size_t)(j * (int64_t)m.size() / k)];
+            qo[j] = src->q_off[i]; to[j] = src->t_off[i]; ql[j] = src->q_len[i]; tl[j] = src->t_len[i];
+        }
+        b = *src;
+        b.n_pairs = k;
+        b.q_off = qo.data(); b.t_off = to.data(); b.q_len = ql.data(); b.t_len = tl.data();
+    }
+};
+
+// A variant other than the default must win by this much to be taken.
+constexpr float kMargin = 0.97f;
+
+int tune_run(agatha_ctx *ctx, const agatha_batch *b, const DevParams &p, uint32_t flags, cudaStream_t s,
+             const LaunchPlan &lp, TuneChoice *choice) {
+    if (!ctx->tune_ev0 && (cudaEventCreate(&ctx->tune_ev0) != cudaSuccess ||
+                           cudaEventCreate(&ctx->tune_ev1) != cudaSuccess)) {
+        cudaGetLastError();
+        return set_error(ctx, AGATHA_ECUDA, "tuning events");
+    }
+    std::vector<std::vector<int64_t>> members(N_CLASSES);
+    std::vector<int64_t> all;
+    for (int64_t i = 0; i < b->n_pairs; ++i) {
+        const int32_t tl = b->t_len[i], ql = b->q_len[i];
+        if (tl <= 0 || ql <= 0) continue;
+        const int32_t w = effective_w(p.w, tl, ql);
+        if (w > lp.warp_w_max) continue;             // aligned by the block kernel
+        members[class_of_cells(predicted_cells(tl, ql, w))].push_back(i);
+        all.push_back(i);
+    }
+    std::vector<agatha_result> res(std::min<int64_t>(std::max<int64_t>((int64_t)all.size(), 1), kTuneSplitPairs));
+    // 1. each class on its own: the fastest variant
+    bool any_other = false;
+    for (int c = 0; c < N_CLASSES; ++c) {
+        choice->var[c] = VAR_16;
+        if (members[c].empty()) continue;
+        SubBatch sb(b, members[c], kTuneMaxPairs);
+        float t_default = 0.f;
+        float best = 0.f;
+        for (int v = 0; v < N_VARIANTS; ++v) {
+            float ms = 0.f;
+            const int rc = time_plan(ctx, sb.b, p, flags, s, single_variant(lp, v), res, &ms);
+            if (rc) return rc;
+            if (v == VAR_16) {
+                t_default = best = ms;
+            } else if (ms < best && ms < kMargin * t_default) {
+                best = ms;
+                choice->var[c] = (int8_t)v;
+            }
+        }
+        any_other |= choice->var[c] != VAR_16;
+    }
+    // 2. one launch per class costs its own tails: keep it only if the batch
+    //    (up to kTuneSplitPairs of it) runs faster that way than as one launch
+    choice->split = 0;
+    if (any_other && !all.empty()) {
+        SubBatch sb(b, all, kTuneSplitPairs);
+        LaunchPlan split = lp;
+        split.split = 1;
+        for (int c = 0; c < N_CLASSES; ++c) split.cls_var[c] = choice->var[c];
+        float t_one = 0.f, t_split = 0.f;
+        int rc = time_plan(ctx, sb.b, p, flags, s, single_variant(lp, VAR_16), res, &t_one);
+        if (!rc) rc = time_plan(ctx, sb.b, p, flags, s, split, res, &t_split);
+        if (rc) return rc;
+        choice->split = t_split < kMargin * t_one ? 1 : 0;
+    }
+    return AGATHA_OK;
+}
+
+}  // namespace
+
+void tune_load(agatha_ctx *ctx) {
+    if (ctx->tune_cache_path.empty()) return;
+    std::ifstream f(ctx->tune_cache_path);
+    std::string line;
+    while (f && std::getline(f, line)) {
+        std::istringstream is(line);
+        std::string key;
+        TuneChoice v;
+        bool ok = (bool)(is >> key);
+        for (int c = 0; ok && c < N_CLASSES; ++c) {
+            int x = -1;
+            ok = (bool)(is >> x) && x >= 0 && x < N_VARIANTS;
+            v.var[c] = (int8_t)x;
+        }
+        int sp = -1;
+        ok = ok && (bool)(is >> sp) && (sp == 0 || sp == 1);
+        v.split = (int8_t)sp;
+        if (ok) ctx->tune_table[key] = v;        // malformed lines are ignored
+    }
+}
+
+int tune_apply(agatha_ctx *ctx, const agatha_batch *batch, const DevParams &p, uint32_t flags,
+               cudaStream_t s, LaunchPlan *lp) {
+    const uint32_t off = AGATHA_NO_TUNE | AGATHA_PLAIN | AGATHA_FORCE32 | AGATHA_NO_SORT | AGATHA_REGS_HIGH;
+    if (!ctx->autotune || (flags & off) || lp->plain || !lp->lane16 || !lp->sort) return AGATHA_OK;
+    const std::string key = tune_key(ctx, p, lp->C16);
+    auto it = ctx->tune_table.find(key);
+    if (it == ctx->tune_table.end()) {
+        if (flags & AGATHA_DEVICE_PTRS) return AGATHA_OK;   // lengths on the device: default plan
+        TuneChoice choice;
+        const int rc = tune_run(ctx, batch, p, flags, s, *lp, &choice);
+        if (rc) return rc;
+        it = ctx->tune_table.emplace(key, choice).first;
+        tune_save(ctx);
+    }
+    if (!it->second.split) return AGATHA_OK;    // one launch measured faster
+    lp->split = 1;
+    for (int c = 0; c < N_CLASSES; ++c) lp->cls_var[c] = it->second.var[c];
+    return AGATHA_OK;
+}
+
+}  // namespace agatha
+
+using namespace agatha;
+
+extern "C" int agatha_tune_variants(agatha_ctx *ctx, const agatha_params *params, int32_t w_max,
+                                    int32_t *variants) {
+    if (!ctx || !params || !variants) return AGATHA_EINVAL;
+    DevParams p;
+    if (normalise_params(params, &p)) return AGATHA_EINVAL;
+    const int32_t w = w_max < 0 ? 32 * 32 - 1 : w_max;
+    const int C16 = pick_slots16(w);
+    if (C16 == 0 || step_change_max(p) > 64) return AGATHA_ENOTSUP;
+    std::lock_guard<std::mutex> lock(ctx->mu);
+    auto it = ctx->tune_table.find(tune_key(ctx, p, C16));
+    if (it == ctx->tune_table.end()) return AGATHA_EAGAIN;
+    for (int c = 0; c < N_CLASSES; ++c) variants[c] = it->second.var[c];
+    variants[N_CLASSES] = it->second.split;
+    return AGATHA_OK;
+}

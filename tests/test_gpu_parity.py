@@ -23,6 +23,8 @@ PATHS = {
     "no_graph": A.AGATHA_NO_GRAPH,
     "force32": A.AGATHA_FORCE32,
     "force32_edge": A.AGATHA_FORCE32 | A.AGATHA_EDGE_PATH_ONLY,
+    "regs_high": A.AGATHA_REGS_HIGH,
+    "regs_high_edge": A.AGATHA_REGS_HIGH | A.AGATHA_EDGE_PATH_ONLY,
 }
 
 
@@ -94,7 +96,7 @@ def test_adversarial_pairs(ctx, si):
     scoring = ADVERSARIAL_SCORINGS[si]
     batch = _adversarial_batch(np.random.default_rng(100 + si), scoring)
     ref = O.align_batch(batch)
-    for path in ("batched", "plain", "edge_only", "force32"):
+    for path in ("batched", "plain", "edge_only", "force32", "regs_high"):
         got = A.agatha_align_batch(ctx, batch, flags=PATHS[path])
         _assert_same(got, ref, batch, f"adversarial[{si}]/{path}")
 
