@@ -14,6 +14,8 @@ w=500, zdrop=400).  Printed as one JSON line:
   roofline    the warp kernel against the integer issue rate of the GPU
   cpu_baseline the CPU oracle on a bounded sample of the same workload
 
+``--workload hifi|skewed|small`` measures another configuration with the same
+metric (the ONT-like batch is the default and the headline).
 ``--impl reference`` times the CPU oracle as the reference arm instead.
 Multi-GPU (torchrun): every rank aligns its own batch (weak scaling, no
 collective on the data path); rank 0 prints the aggregate.
@@ -35,9 +37,19 @@ sys.path.insert(0, ROOT)
 import numpy as np  # noqa: E402
 
 METRIC = "GCUPS & pairs/s on ONT-like mix: batched vs plain GPU kernel, bit-exact"
-WORKLOAD = ("ont: 20000 pairs, query log-normal (median 5 kbp, sigma 0.8, clip 500-50k), "
+WORKLOADS = {
+    "ont": ("ont: 20000 pairs, query log-normal (median 5 kbp, sigma 0.8, clip 500-50k), "
             "target 5% sub / 4% del / 3% ins, 10% divergent tails, a=2 b=4 q=4 e=2 q2=24 e2=1, "
-            "w=500, zdrop=400")
+            "w=500, zdrop=400"),
+    "hifi": ("hifi: 20000 pairs, query Normal(15 kbp, 3 kbp) min 2 kbp, 1% errors "
+             "(0.5 sub / 0.25 ins / 0.25 del), 2% divergent tails, a=1 b=4 q=6 e=2 q2=26 e2=1, "
+             "w=500, zdrop=200"),
+    "skewed": ("skewed: 100000 pairs, query Pareto(alpha 1.5, min 500 bp, cap 100 kbp), 8% errors "
+               "(4 sub / 2 ins / 2 del), 20% divergent tails, a=2 b=4 q=4 e=2 q2=24 e2=1, w=750, "
+               "zdrop=400"),
+    "small": ("small: 256 pairs of 1000 bp, 5% sub / 2.5% ins / 2.5% del, a=2 b=4 q=4 e=2 "
+              "q2=24 e2=1, w=100, zdrop=400"),
+}
 L2_FLUSH_BYTES = 512 << 20          # > 129 MB of L2
 # algorithmic integer lane-ops per band cell (substitution score 2, five-way
 # max 3, two gap openings 2, four gap add-max 4, max tracking 2); a packed
@@ -45,6 +57,7 @@ L2_FLUSH_BYTES = 512 << 20          # > 129 MB of L2
 OPS_PER_CELL_I32 = 13.0
 OPS_PER_CELL_I16X2 = 6.5
 CPU_SAMPLE_PAIRS = 6000
+CPU_SAMPLE_CELLS = 4e10             # about 12 s of the oracle on 16 cores
 REF_STEP_PAIRS = 300
 
 
@@ -141,8 +154,12 @@ def _kernel_digest():
 
 def cpu_baseline(batch, n_sample: int, seed: int = 7):
     from oracle import oracle as O      # the CPU oracle: timed here as a reported baseline
+    from paper_2403_06478_gb300 import shard as S
     rng = np.random.default_rng(seed)
-    idx = np.sort(rng.choice(batch.n_pairs, min(n_sample, batch.n_pairs), replace=False))
+    idx = rng.permutation(batch.n_pairs)[:n_sample]
+    # bounded: stop adding pairs once the predicted work reaches CPU_SAMPLE_CELLS
+    est = np.cumsum(S.predicted_cells(batch.q_len[idx], batch.t_len[idx], batch.scoring.w))
+    idx = np.sort(idx[:max(1, int(np.searchsorted(est, CPU_SAMPLE_CELLS)) + 1)])
     cores = os.cpu_count() or 1
     O.align_batch(batch, idx=idx[:8], threads=cores)     # load + warm
     t0 = time.perf_counter()
@@ -160,7 +177,7 @@ def run_reference(args):
         return 0
     from paper_2403_06478_gb300 import workload as W
     from oracle import oracle as O
-    batch = W.make_config("ont")
+    batch = W.make_config(args.workload)
     cores = os.cpu_count() or 1
     rng = np.random.default_rng(11)
     perm = rng.permutation(batch.n_pairs)
@@ -186,7 +203,8 @@ def run_reference(args):
         "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": round(total_s / max(args.steps, 1) * 1e3, 3), "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "int64", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "step": f"{REF_STEP_PAIRS} pairs per step (bounded sample)"},
+        "config": {"workload": WORKLOADS[args.workload],
+                   "step": f"{REF_STEP_PAIRS} pairs per step (bounded sample)"},
         "pairs_per_s": round(total_pairs / total_s, 2),
         "cpu_baseline": {"value": round(gcups, 4), "unit": "GCUPS", "cores": cores, "kind": "oracle",
                          "sample": f"{args.steps} steps x {REF_STEP_PAIRS} seeded random pairs"},
@@ -206,6 +224,8 @@ def main():
     ap.add_argument("--plain-steps", type=int, default=3)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-sample-pairs", type=int, default=CPU_SAMPLE_PAIRS)
+    ap.add_argument("--workload", default="ont", choices=sorted(WORKLOADS),
+                    help="ont (the headline), or another configuration of the same metric")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     if args.impl == "reference":
@@ -225,7 +245,7 @@ def main():
     B.build()
 
     # each rank aligns its own batch: rank 0 the standard workload, others reseeded
-    batch = W.make_config("ont", seed=None if rank == 0 else W.SEED_BASE + 2 + 1000 * rank)
+    batch = W.make_config(args.workload, seed=None if rank == 0 else W.SEED_BASE + 2 + 1000 * rank)
     pb = A.pack_batch(batch)
     n = pb.n_pairs
     ctx = A.Context(local, timing=True, autotune=True)
@@ -334,7 +354,7 @@ def main():
         "ms_per_step": round(tot_ms / args.steps, 3), "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "int16x2" if cells16 * 2 > cells else "int32",
         "data": "synthetic",
-        "config": {"workload": WORKLOAD, "pairs_per_gpu": n, "cells_per_step": cells,
+        "config": {"workload": WORKLOADS[args.workload], "pairs_per_gpu": n, "cells_per_step": cells,
                    "pairs_on_16bit_lanes": int(lane16.sum()),
                    "autotune": None if tuned is None else
                    {"class_variants": [A.VARIANT_NAMES[v] for v in tuned[:4]], "split": split},
