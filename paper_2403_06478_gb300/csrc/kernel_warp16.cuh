@@ -193,6 +193,10 @@ struct WarpPair16 {
     __device__ __forceinline__ static uint32_t half_mask(uint32_t bits) {
         return prmt(bits << (15 - PP), 0, 0xbb99);
     }
+    // the same for a register index known only after unrolling
+    __device__ __forceinline__ static uint32_t half_mask_rt(uint32_t bits, int p) {
+        return prmt(bits << (15 - p), 0, 0xbb99);
+    }
     // lane bits of the local slots [lo, hi] (empty if lo > hi)
     __device__ __forceinline__ static uint32_t range_bits(int32_t lo, int32_t hi) {
         lo = max(lo, 0);
@@ -263,31 +267,49 @@ struct WarpPair16 {
         return false;
     }
 
+    // H of the band slot j (the same j in every lane) of the anti-diagonal
+    // just computed, read from the lane that owns it.
+    __device__ __forceinline__ int32_t slot_value(const uint32_t (&Hn)[P], int32_t j) const {
+        const int32_t local = j % C, pl = local % P;
+        uint32_t v = Hn[0];
+#pragma unroll
+        for (int p = 1; p < P; ++p) v = pl == p ? Hn[p] : v;
+        const int32_t h = local >= P ? (int32_t)(v >> 16) : (int32_t)(v & 0xffffu);
+        return __shfl_sync(FULL, h, j / C);
+    }
+
+    // Step modes.  BULK: every slot in [0, w] is a band cell of the table.
+    // HEAD (r <= w + 1): the band meets the table's first row and column;
+    // after the update every slot is set to what the recurrence defines
+    // there: a band cell keeps its value, the virtual row/column cell
+    // (-1, r+1) or (r+1, -1) gets H = -gap(r+2) (H(-1,-1) = 0 on r = -2),
+    // anything else is minus infinity.  TAIL (r >= w + 2): the band may run
+    // past the last row or column.  Cells there (t >= tlen or q >= qlen) feed
+    // only cells past the end again, never a cell of the table, so they are
+    // left as computed and only kept out of the maximum.
+    enum : int { BULK = 0, HEAD = 1, TAIL = 2 };
+
     // One anti-diagonal on the packed registers, in place (H(r) replaces
     // H(r-2) in the array of its parity, the gap arrays turn from the states
     // leaving r-1 into those leaving r).  ODD: (r - w) odd, E from slot j-1
     // and F from slot j; else E from slot j and F from slot j+1.  F-from-j+1
     // steps walk the registers upwards and E-from-j-1 steps downwards, so
     // every old value is read before it is overwritten.
-    //
-    // MASKED: the band meets the table's edges on r.  After the update every
-    // slot is set to what the recurrence defines there: a band cell keeps its
-    // value, the virtual row/column cell (-1, r+1) or (r+1, -1) gets
-    // H = -gap(r+2) (H(-1,-1) = 0 on r = -2), anything else is minus infinity.
-    template <bool ODD, bool MASKED>
+    template <bool ODD, int MODE>
     __device__ __forceinline__ bool step(int32_t r) {
         uint32_t (&Hd)[P] = ODD ? Hod : Hev;
         const int32_t B = frame(r);
         int32_t st = 0, en = -1;
-        uint32_t rb = 0, vb = 0, tb = 0, qb = 0, VVp = 0, VVe = 0, VVe2 = 0;
-        bool te_real = false, qe_real = false;
-        if constexpr (MASKED) {
+        uint32_t rb = 0, vb = 0, VVp = 0, VVe = 0, VVe2 = 0;
+        if constexpr (MODE != BULK) {
             if (r >= 0) {
                 st = max(max(0, r - qlen + 1), ceil_div2(r - w));
                 en = min(min(tlen - 1, r), floor_div2(r + w));
                 if (st > en) { zdropped = 1; return true; }  // the band left the table
             }
             rb = range_bits(st - B - j0, en - B - j0);
+        }
+        if constexpr (MODE == HEAD) {
             if (r + 1 < qlen) vb |= slot_bit(-1 - B - j0);                 // (-1, r+1)
             if (r >= -1 && r + 1 < tlen) vb |= slot_bit(r + 1 - B - j0);  // (r+1, -1)
             const int32_t vv = to_u(r == -2 ? 0 : -gap_cost(prm, r + 2));
@@ -295,10 +317,6 @@ struct WarpPair16 {
             VVp = (uint32_t)vv * 0x10001u;
             VVe = (uint32_t)(vv - oe) * 0x10001u;
             VVe2 = (uint32_t)(vv - oe2) * 0x10001u;
-            te_real = r >= 0 && st <= tlen - 1 && tlen - 1 <= en;
-            qe_real = r >= 0 && st <= r - qlen + 1 && r - qlen + 1 <= en;
-            tb = te_real ? slot_bit(tlen - 1 - B - j0) : 0u;
-            qb = qe_real ? slot_bit(r - qlen + 1 - B - j0) : 0u;
         }
         uint32_t edge, edge2;
         if constexpr (ODD) {
@@ -313,7 +331,7 @@ struct WarpPair16 {
             const uint32_t fR = __shfl_down_sync(FULL, Fo[0], 1);
             const uint32_t f2R = __shfl_down_sync(FULL, F2o[0], 1);
             uint32_t inj = NEGp, inj2 = NEGp;
-            if (MASKED && lane == 31) {
+            if (MODE == HEAD && lane == 31) {
                 // beyond the last lane: slot 32C of r-1, the virtual column
                 // cell (t, -1) when q == -1 there
                 const int32_t ts = frame(r - 1) + 32 * C, qs = r - 1 - ts;
@@ -328,7 +346,7 @@ struct WarpPair16 {
             edge2 = mux(L31HI, inj2, prmt(F2o[0], f2R, 0x5432));
         }
         const Comb comb = packed_mismatch();
-        uint32_t lmax = 0, tmax = 0, qmax = 0, pend = 0;
+        uint32_t lmax = 0, pend = 0;
 #pragma unroll
         for (int i = 0; i < P; ++i) {
             const int p = ODD ? P - 1 - i : i;
@@ -350,7 +368,8 @@ struct WarpPair16 {
             // H = max(H(r-2) + s, E, F, E2, F2): add-max, 3-input max, max
             const uint32_t H = __vmaxu2(__vimax3_u16x2(__viaddmax_u16x2(Hd[p], s2, Ein), Fin, E2in),
                                         F2in);
-            if constexpr (!MASKED) {
+            uint32_t mx;                          // this register's share of the maximum
+            if constexpr (MODE != HEAD) {
                 const uint32_t dead = dead_mask_r<ODD>(p);
                 const uint32_t hoe = mux(dead, NEGp, H - OEp);
                 const uint32_t hoe2 = hoe - DOEp;
@@ -360,15 +379,12 @@ struct WarpPair16 {
                 E2o[p] = __viaddmax_u16x2(E2in, NE2p, hoe2);
                 F2o[p] = __viaddmax_u16x2(F2in, NE2p, hoe2);
                 Hd[p] = H;
-                // running maximum, two registers per 3-input max
-                if (i & 1) lmax = __vimax3_u16x2(lmax, pend, hoe);
-                else if (i == P - 1) lmax = __vmaxu2(lmax, hoe);
-                else pend = hoe;
+                mx = MODE == BULK ? hoe : (half_mask_rt(rb, p) & hoe);
             } else {
                 const uint32_t hoe = H - OEp;
                 const uint32_t hoe2 = hoe - DOEp;
-                const uint32_t rm = prmt(rb << (15 - p), 0, 0xbb99);
-                const uint32_t vm = prmt(vb << (15 - p), 0, 0xbb99);
+                const uint32_t rm = half_mask_rt(rb, p);
+                const uint32_t vm = half_mask_rt(vb, p);
                 const uint32_t fillE = mux(vm, VVe, NEGp);
                 const uint32_t fillE2 = mux(vm, VVe2, NEGp);
                 Eo[p] = mux(rm, __viaddmax_u16x2(Ein, NEp, hoe), fillE);
@@ -376,12 +392,14 @@ struct WarpPair16 {
                 E2o[p] = mux(rm, __viaddmax_u16x2(E2in, NE2p, hoe2), fillE2);
                 F2o[p] = mux(rm, __viaddmax_u16x2(F2in, NE2p, hoe2), fillE2);
                 Hd[p] = mux(rm, H, mux(vm, VVp, NEGp));
-                lmax = __vmaxu2(lmax, rm & hoe);
-                tmax = __vmaxu2(tmax, prmt(tb << (15 - p), 0, 0xbb99) & H);
-                qmax = __vmaxu2(qmax, prmt(qb << (15 - p), 0, 0xbb99) & H);
+                mx = rm & hoe;
             }
+            // running maximum, two registers per 3-input max
+            if (i & 1) lmax = __vimax3_u16x2(lmax, pend, mx);
+            else if (i == P - 1) lmax = __vmaxu2(lmax, mx);
+            else pend = mx;
         }
-        if constexpr (!MASKED) {
+        if constexpr (MODE == BULK) {
             // (the band cells of bulk anti-diagonals are counted by run())
             return anti_diagonal_max<ODD>(r, B, lmax, Hd, [&](int p) { return dead_mask_r<ODD>(p); });
         } else {
@@ -391,24 +409,23 @@ struct WarpPair16 {
             // best score on the last target row / the last query column
             bool set_gs = false;
             int32_t gs = K_NEG_OUT;
-            if (te_real) {
-                const int32_t tv = to_true(
-                    __reduce_max_sync(FULL, (int32_t)max(tmax & 0xffffu, tmax >> 16)));
+            if (st <= tlen - 1 && tlen - 1 <= en) {
+                const int32_t tv = to_true(slot_value(Hd, tlen - 1 - B));
                 if (tv > cold.mte && lane == 0) { cold.mte = tv; cold.mte_q = r - (tlen - 1); }
                 if (r == last_r) { gs = tv; set_gs = true; }   // kept unless Z-drop stops r
             }
-            if (qe_real) {
-                const int32_t qv = to_true(
-                    __reduce_max_sync(FULL, (int32_t)max(qmax & 0xffffu, qmax >> 16)));
+            if (st <= r - qlen + 1 && r - qlen + 1 <= en) {
+                const int32_t qv = to_true(slot_value(Hd, r - qlen + 1 - B));
                 if (qv > cold.mqe && lane == 0) { cold.mqe = qv; cold.mqe_t = r - (qlen - 1); }
             }
             __syncwarp();
-            if (anti_diagonal_max<ODD>(r, B, lmax, Hd, [&](int p) {
-                    return ~prmt(rb << (15 - p), 0, 0xbb99);
-                }))
+            if (anti_diagonal_max<ODD>(r, B, lmax, Hd, [&](int p) { return ~half_mask_rt(rb, p); }))
                 return true;
             if (set_gs && lane == 0) cold.gscore = gs;
-            if (--until_rebase <= 2) rebase(last_m, r);
+            if (--until_rebase <= 2) {
+                if (MODE == TAIL) rebase(last_m, r, rb, table_bits(r - 1));
+                else rebase(last_m, r);      // head: slots off the table hold NEG already
+            }
             return ovf;
         }
     }
@@ -417,9 +434,9 @@ struct WarpPair16 {
     // k+1 when the extension stopped on r+k.
     __device__ __forceinline__ int fast_pair(int32_t r) {
         shift_t();
-        if (step<false, false>(r)) return 1;
+        if (step<false, BULK>(r)) return 1;
         shift_q();
-        if (step<true, false>(r + 1)) return 2;
+        if (step<true, BULK>(r + 1)) return 2;
         until_rebase -= 2;
         if (until_rebase <= 2) {
             rebase(last_m, r + 1);
@@ -428,8 +445,11 @@ struct WarpPair16 {
         return 0;
     }
 
-    __device__ __forceinline__ bool masked_step(int32_t r) {
-        return ((r - w) & 1) ? step<true, true>(r) : step<false, true>(r);
+    __device__ __forceinline__ bool head_step(int32_t r) {
+        return ((r - w) & 1) ? step<true, HEAD>(r) : step<false, HEAD>(r);
+    }
+    __device__ __forceinline__ bool tail_step(int32_t r) {
+        return ((r - w) & 1) ? step<true, TAIL>(r) : step<false, TAIL>(r);
     }
 
     // ---------------------------------------------------------------- rebase
@@ -446,18 +466,24 @@ struct WarpPair16 {
         x = (uint32_t)lo | ((uint32_t)hi << 16);
     }
     // r: the last anti-diagonal computed (its gap states are in Eo..)
-    __device__ __forceinline__ void rebase(int32_t m_u, int32_t r) {
+    // in_r / in_r1: lane bits of the slots of anti-diagonals r / r-1 that are
+    // cells of the table; the others (past the table's end in the tail) are
+    // reset like the slots beyond the band and not checked.
+    __device__ __forceinline__ void rebase(int32_t m_u, int32_t r, uint32_t in_r = ~0u,
+                                           uint32_t in_r1 = ~0u) {
         until_rebase = kint;
         const int32_t delta = m_u - OFF;
         const int32_t low = LOWCHK - Dp + delta;
         const bool odd = ((r - w) & 1) != 0;
+        const uint32_t in_ev = odd ? in_r1 : in_r, in_od = odd ? in_r : in_r1;
 #pragma unroll
         for (int p = 0; p < P; ++p) {
             const uint32_t dm = dead_mask(p);
-            const uint32_t dm_odd = p == 0 ? (dm | L0LO) : dm;
-            const uint32_t dm_r = odd ? dm_odd : dm;           // slots of anti-diagonal r
-            rebase_reg(Hev[p], dm, delta, low);
-            rebase_reg(Hod[p], dm_odd, delta, low);
+            const uint32_t dm_ev = dm | ~half_mask_rt(in_ev, p);
+            const uint32_t dm_od = (p == 0 ? (dm | L0LO) : dm) | ~half_mask_rt(in_od, p);
+            const uint32_t dm_r = odd ? dm_od : dm_ev;         // slots of anti-diagonal r
+            rebase_reg(Hev[p], dm_ev, delta, low);
+            rebase_reg(Hod[p], dm_od, delta, low);
             rebase_reg(Eo[p], dm_r, delta, low);
             rebase_reg(E2o[p], dm_r, delta, low);
             rebase_reg(Fo[p], dm_r, delta, low);
@@ -465,6 +491,13 @@ struct WarpPair16 {
         }
         base += delta;
         if (__any_sync(FULL, ovf)) ovf = true;
+    }
+    // lane bits of the table's cells among the slots of anti-diagonal r
+    __device__ __forceinline__ uint32_t table_bits(int32_t r) const {
+        const int32_t st = max(max(0, r - qlen + 1), ceil_div2(r - w));
+        const int32_t en = min(min(tlen - 1, r), floor_div2(r + w));
+        const int32_t B = frame(r);
+        return range_bits(st - B - j0, en - B - j0);
     }
 
     // ------------------------------------------------------------------ pair
@@ -521,12 +554,12 @@ struct WarpPair16 {
 
         int32_t r = -2;
         init_windows(r);
-        bool stop = masked_step(r);
+        bool stop = head_step(r);
         const int32_t head_end = min(last_r, w + 1);
         while (!stop && r < head_end) {
             ++r;
             advance(r);
-            stop = masked_step(r);
+            stop = head_step(r);
         }
         // bulk: pairs starting at r = w + 2 ((r - w) even) while every band
         // cell of the pair is a real cell away from the last row and column
@@ -548,10 +581,10 @@ struct WarpPair16 {
             const int32_t nb = r - r0;
             cells += (int64_t)(nb >> 1) * (2 * w + 1) + (int64_t)(nb & 1) * (w + 1);
         }
-        while (!stop && r < last_r) {
+        while (!stop && r < last_r) {     // r > w + 1 here
             ++r;
             advance(r);
-            stop = masked_step(r);
+            stop = tail_step(r);
         }
         if (ovf) return false;
         if (lane == 0) {
