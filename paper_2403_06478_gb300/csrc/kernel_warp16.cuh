@@ -401,7 +401,11 @@ struct WarpPair16 {
         }
         if constexpr (MODE == BULK) {
             // (the band cells of bulk anti-diagonals are counted by run())
-            return anti_diagonal_max<ODD>(r, B, lmax, Hd, [&](int p) { return dead_mask_r<ODD>(p); });
+            // slots beyond the band sit above every band slot of their lane, so
+            // the lowest slot holding the maximum is a band slot; only slot 0 of
+            // lane 0 (below the band on odd anti-diagonals) is excluded
+            return anti_diagonal_max<ODD>(r, B, lmax, Hd,
+                                          [&](int p) { return (ODD && p == 0) ? L0LO : 0u; });
         } else {
             if (__any_sync(FULL, ovf)) { ovf = true; return true; }
             if (r < 0) return false;
@@ -456,14 +460,16 @@ struct WarpPair16 {
     // Move base so that the anti-diagonal maximum m_u is stored at OFF; check
     // that every band score keeps (K+3)D of headroom above NEG; reset minus
     // infinity (anything at most NEG) and slots outside the band to NEG.
-    __device__ __forceinline__ void rebase_reg(uint32_t &x, uint32_t dm, int32_t delta, int32_t low) {
-        int32_t lo = (int32_t)(x & 0xffffu), hi = (int32_t)(x >> 16);
-        const bool dlo = dm & 1u, dhi = dm >> 31;
-        if (dlo || lo <= (int32_t)U_NEG) lo = (int32_t)U_NEG;
-        else { if (lo < low) ovf = true; lo = min(max(lo - delta, (int32_t)U_NEG + 1), 0xffff); }
-        if (dhi || hi <= (int32_t)U_NEG) hi = (int32_t)U_NEG;
-        else { if (hi < low) ovf = true; hi = min(max(hi - delta, (int32_t)U_NEG + 1), 0xffff); }
-        x = (uint32_t)lo | ((uint32_t)hi << 16);
+    // Both halves of x at once: halves of dm (0xFFFF) and halves at most NEG
+    // become NEG; the others must be at least `low2` (else ovf) and move by
+    // -delta, clamped to [NEG + 1, 0xFFFF] (sub: delta >= 0, by d2 = delta;
+    // else by d2 = -delta upwards).
+    template <bool SUB>
+    __device__ __forceinline__ void rebase_reg(uint32_t &x, uint32_t dm, uint32_t d2, uint32_t low2) {
+        const uint32_t reset = __vcmpleu2(x, NEGp) | dm;
+        if (__vcmpltu2(x, low2) & ~reset) ovf = true;
+        const uint32_t y = __vmaxu2(SUB ? __vsubus2(x, d2) : __vaddus2(x, d2), NEGp + 0x10001u);
+        x = mux(reset, NEGp, y);
     }
     // r: the last anti-diagonal computed (its gap states are in Eo..)
     // in_r / in_r1: lane bits of the slots of anti-diagonals r / r-1 that are
@@ -473,24 +479,31 @@ struct WarpPair16 {
                                            uint32_t in_r1 = ~0u) {
         until_rebase = kint;
         const int32_t delta = m_u - OFF;
-        const int32_t low = LOWCHK - Dp + delta;
+        const int32_t low = min(max(LOWCHK - Dp + delta, 0), 0xffff);
+        const uint32_t low2 = (uint32_t)low * 0x10001u;
         const bool odd = ((r - w) & 1) != 0;
         const uint32_t in_ev = odd ? in_r1 : in_r, in_od = odd ? in_r : in_r1;
+        if (delta >= 0) rebase_all<true>((uint32_t)min(delta, 0xffff) * 0x10001u, low2, odd, in_ev, in_od);
+        else rebase_all<false>((uint32_t)min(-delta, 0xffff) * 0x10001u, low2, odd, in_ev, in_od);
+        base += delta;
+        if (__any_sync(FULL, ovf)) ovf = true;
+    }
+    template <bool SUB>
+    __device__ __forceinline__ void rebase_all(uint32_t d2, uint32_t low2, bool odd, uint32_t in_ev,
+                                               uint32_t in_od) {
 #pragma unroll
         for (int p = 0; p < P; ++p) {
             const uint32_t dm = dead_mask(p);
             const uint32_t dm_ev = dm | ~half_mask_rt(in_ev, p);
             const uint32_t dm_od = (p == 0 ? (dm | L0LO) : dm) | ~half_mask_rt(in_od, p);
             const uint32_t dm_r = odd ? dm_od : dm_ev;         // slots of anti-diagonal r
-            rebase_reg(Hev[p], dm_ev, delta, low);
-            rebase_reg(Hod[p], dm_od, delta, low);
-            rebase_reg(Eo[p], dm_r, delta, low);
-            rebase_reg(E2o[p], dm_r, delta, low);
-            rebase_reg(Fo[p], dm_r, delta, low);
-            rebase_reg(F2o[p], dm_r, delta, low);
+            rebase_reg<SUB>(Hev[p], dm_ev, d2, low2);
+            rebase_reg<SUB>(Hod[p], dm_od, d2, low2);
+            rebase_reg<SUB>(Eo[p], dm_r, d2, low2);
+            rebase_reg<SUB>(E2o[p], dm_r, d2, low2);
+            rebase_reg<SUB>(Fo[p], dm_r, d2, low2);
+            rebase_reg<SUB>(F2o[p], dm_r, d2, low2);
         }
-        base += delta;
-        if (__any_sync(FULL, ovf)) ovf = true;
     }
     // lane bits of the table's cells among the slots of anti-diagonal r
     __device__ __forceinline__ uint32_t table_bits(int32_t r) const {
