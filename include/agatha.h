@@ -184,21 +184,22 @@ int agatha_pack_ascii(const char *ascii, int64_t n, uint32_t *out);
  * (w < 0: unbanded): the work estimate used for scheduling. */
 int64_t agatha_band_cells(int32_t tlen, int32_t qlen, int32_t w);
 
-/* Autotuner.  With AGATHA_CFG_AUTOTUNE the batched path may split the
- * ordered queue into four length classes by predicted band cells (the
- * Section 4.5 model: >= 2^25, >= 2^23, >= 2^21, smaller) and launch one
- * kernel per class.  The variant of each class (0: 16-bit lanes, 1: 16-bit
- * lanes at the larger register budget, 2: int32 lanes) is measured the first
- * time a host batch arrives for a scoring and band class, on up to 4096 of
- * its pairs per class; a non-default variant must be 3% faster, and the split
- * is kept only if the batch (up to 32768 of its pairs) runs 3% faster split
- * than as one launch.  Choices are kept per context and in tune_cache_path (one line
- * per key, read at agatha_init).  Every variant gives bit-identical results.
- * agatha_tune_variants writes what was tuned for `params` (band half-width
- * w_max: the widest effective band of the batches) into variants[0..4]: the
- * four class variants, then 1 if the split is used.  AGATHA_OK, AGATHA_EAGAIN
- * if not tuned yet, AGATHA_ENOTSUP if 16-bit lanes do not apply to these
- * parameters (nothing to choose). */
+/* Autotuner.  With AGATHA_CFG_AUTOTUNE the first host batch for a scoring
+ * and band class is used to choose the kernel plan by measurement.  Each of
+ * four length classes by predicted band cells (the Section 4.5 model:
+ * >= 2^25, >= 2^23, >= 2^21, smaller; up to 4096 pairs each) is timed with
+ * each variant (0: 16-bit lanes, 1: 16-bit lanes at the larger register
+ * budget, 2: int32 lanes).  If a class prefers another variant, the batch
+ * (up to 131072 of its pairs) is timed as one launch of each winning variant
+ * and, if the classes disagree, with one launch per class.  The fastest plan
+ * is kept (anything but one launch of variant 0 must win by 3%), per context
+ * and in tune_cache_path (one line per key, read at agatha_init).  Every
+ * variant gives bit-identical results.  agatha_tune_variants writes what was
+ * tuned for `params` (band half-width w_max: the widest effective band of
+ * the batches) into variants[0..4]: the four class variants (all equal when
+ * one launch is used), then 1 if one launch per class is used.  AGATHA_OK,
+ * AGATHA_EAGAIN if not tuned yet, AGATHA_ENOTSUP if 16-bit lanes do not apply
+ * to these parameters (nothing to choose). */
 int agatha_tune_variants(agatha_ctx *ctx, const agatha_params *params, int32_t w_max,
                          int32_t *variants);
 

@@ -84,7 +84,9 @@ struct Cold16 {
     int32_t mqe, mqe_t, mte, mte_q, gscore;
 };
 
-template <int C>
+// DMREG: keep the dead-slot masks in registers (the larger register budget)
+// instead of recomputing them at every use.
+template <int C, bool DMREG>
 struct WarpPair16 {
     static_assert(C == 8 || C == 16 || C == 24, "16-bit lanes use 8, 16 or 24 slots per lane");
     static constexpr int P = C / 2;
@@ -108,6 +110,7 @@ struct WarpPair16 {
     // slots beyond the band (j > w): local slots k0.. of this lane, held as
     // (k0 - 1) in both halves so that dead_mask() is one add and one prmt
     uint32_t DF2;
+    uint32_t DMR[DMREG ? P : 1];   // DMREG: dead_mask(p), computed once per pair
     // base windows (2 bits per slot): Tw field jl = T[B + j0 + jl],
     // Qw field jl = Q[r - B - j0 - jl]
     Win Tw, Qw;
@@ -214,6 +217,7 @@ struct WarpPair16 {
     // (k0 - 1 - slot) is negative exactly there (a borrow out of the low half
     // only reaches a high half that is beyond the band as well)
     __device__ __forceinline__ uint32_t dead_mask(int p) const {
+        if constexpr (DMREG) return DMR[p];
         return half_sign_of_diff(DF2, (uint32_t)p | ((uint32_t)(p + P) << 16));
     }
     // the same plus slot 0 of lane 0, outside the band on odd anti-diagonals
@@ -556,6 +560,11 @@ struct WarpPair16 {
         {
             const int32_t k0 = min(max(w + 1 - j0, 0), C);     // first local slot beyond the band
             DF2 = (uint32_t)(k0 - 1) * 0x10001u;
+            if constexpr (DMREG) {
+#pragma unroll
+                for (int p = 0; p < P; ++p)
+                    DMR[p] = prmt(DF2 - ((uint32_t)p | ((uint32_t)(p + P) << 16)), 0, 0xbb99);
+            }
         }
         gmax = 0; gt = -1; gq = -1;
         if (lane == 0) {
@@ -631,7 +640,7 @@ warp16_align_kernel(const DevBatch *__restrict__ d_batch, int32_t use_fast, int3
         if (k >= L.end) break;
         const int32_t pair = L.items ? L.items[k] : k;
         if (!L.items && (!pair_valid(B, pair) || !warp_takes(B, pair))) continue;
-        WarpPair16<C> wp(cold[threadIdx.x >> 5]);
+        WarpPair16<C, (MINB < 4 && C <= 16)> wp(cold[threadIdx.x >> 5]);
         if (!wp.run(B, pair, lane, use_fast != 0) && lane == 0) {
             const int32_t slot = atomicAdd(&B.counters[CTR_NOVF], 1);
             B.ovf_list[slot] = pair;

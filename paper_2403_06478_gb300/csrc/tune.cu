@@ -7,10 +7,11 @@
 // chosen per length class, by measurement, the first time a host batch
 // arrives for a scoring and band width: the pairs of each class (up to 4096,
 // spread over the class) are aligned with every variant and the fastest one
-// kept (a variant other than the default must win by 3%).  One launch per
-// class adds the tail of each launch, so the split is kept only if the batch
-// itself (up to 32768 of its pairs) runs at least 3% faster split than as
-// one launch.
+// kept (a variant other than the default must win by 3%).  If any class
+// prefers another variant, the batch itself (up to 131072 of its pairs) is
+// timed as one launch of each winning variant and, if the classes disagree,
+// as one launch per class; the fastest plan is kept (again with a 3% margin
+// for anything but one launch of the default variant).
 // Every variant computes the same exact results, so the choice only moves
 // time.  Choices are kept per context and, with a cache path, in a text file
 // (one line per key: the key, the four class variants and the split flag).
@@ -28,7 +29,7 @@ namespace agatha {
 namespace {
 
 constexpr int64_t kTuneMaxPairs = 4096;       // per class, to pick its variant
-constexpr int64_t kTuneSplitPairs = 32768;    // of the whole batch, to decide the split
+constexpr int64_t kTuneSplitPairs = 131072;   // of the whole batch, to decide the plan
 
 std::string tune_key(const agatha_ctx *ctx, const DevParams &p, int C16) {
     char buf[256];
@@ -119,40 +120,56 @@ int tune_run(agatha_ctx *ctx, const agatha_batch *b, const DevParams &p, uint32_
         all.push_back(i);
     }
     std::vector<agatha_result> res(std::min<int64_t>(std::max<int64_t>((int64_t)all.size(), 1), kTuneSplitPairs));
-    // 1. each class on its own: the fastest variant
-    bool any_other = false;
+    if (all.empty()) return AGATHA_OK;                 // nothing the warp kernels take
+    // 1. each length class on its own (up to kTuneMaxPairs of it): the
+    //    fastest variant per class
+    TuneChoice per;
+    bool wins[N_VARIANTS] = {true, false, false};
     for (int c = 0; c < N_CLASSES; ++c) {
-        choice->var[c] = VAR_16;
+        per.var[c] = VAR_16;
         if (members[c].empty()) continue;
         SubBatch sb(b, members[c], kTuneMaxPairs);
-        float t_default = 0.f;
-        float best = 0.f;
+        float t[N_VARIANTS];
         for (int v = 0; v < N_VARIANTS; ++v) {
-            float ms = 0.f;
-            const int rc = time_plan(ctx, sb.b, p, flags, s, single_variant(lp, v), res, &ms);
+            const int rc = time_plan(ctx, sb.b, p, flags, s, single_variant(lp, v), res, &t[v]);
             if (rc) return rc;
-            if (v == VAR_16) {
-                t_default = best = ms;
-            } else if (ms < best && ms < kMargin * t_default) {
-                best = ms;
-                choice->var[c] = (int8_t)v;
-            }
         }
-        any_other |= choice->var[c] != VAR_16;
+        for (int v = 1; v < N_VARIANTS; ++v)
+            if (t[v] < kMargin * t[per.var[c]]) per.var[c] = (int8_t)v;
+        wins[per.var[c]] = true;
     }
-    // 2. one launch per class costs its own tails: keep it only if the batch
-    //    (up to kTuneSplitPairs of it) runs faster that way than as one launch
     choice->split = 0;
-    if (any_other && !all.empty()) {
-        SubBatch sb(b, all, kTuneSplitPairs);
+    for (int c = 0; c < N_CLASSES; ++c) choice->var[c] = VAR_16;
+    if (!wins[VAR_16_HIGHREG] && !wins[VAR_32]) return AGATHA_OK;   // the default everywhere
+    // 2. the batch itself (up to kTuneSplitPairs of it) as one launch of the
+    //    default and of every variant that won a class, and as one launch per
+    //    class; the fastest plan is kept
+    SubBatch whole(b, all, kTuneSplitPairs);
+    float best = 0.f;
+    int best_v = VAR_16;
+    for (int v = 0; v < N_VARIANTS; ++v) {
+        if (!wins[v]) continue;
+        float t = 0.f;
+        const int rc = time_plan(ctx, whole.b, p, flags, s, single_variant(lp, v), res, &t);
+        if (rc) return rc;
+        if (v == VAR_16) best = t;
+        else if (t < kMargin * best) { best = t; best_v = v; }
+    }
+    for (int c = 0; c < N_CLASSES; ++c) choice->var[c] = (int8_t)best_v;
+    bool mixed = false;
+    for (int c = 1; c < N_CLASSES; ++c) mixed |= per.var[c] != per.var[0];
+    if (mixed) {
+        // one launch per class costs its own tails
         LaunchPlan split = lp;
         split.split = 1;
-        for (int c = 0; c < N_CLASSES; ++c) split.cls_var[c] = choice->var[c];
-        float t_one = 0.f, t_split = 0.f;
-        int rc = time_plan(ctx, sb.b, p, flags, s, single_variant(lp, VAR_16), res, &t_one);
-        if (!rc) rc = time_plan(ctx, sb.b, p, flags, s, split, res, &t_split);
+        for (int c = 0; c < N_CLASSES; ++c) split.cls_var[c] = per.var[c];
+        float t_split = 0.f;
+        const int rc = time_plan(ctx, whole.b, p, flags, s, split, res, &t_split);
         if (rc) return rc;
-        choice->split = t_split < kMargin * t_one ? 1 : 0;
+        if (t_split < kMargin * best) {
+            *choice = per;
+            choice->split = 1;
+        }
     }
     return AGATHA_OK;
 }
@@ -194,7 +211,12 @@ int tune_apply(agatha_ctx *ctx, const agatha_batch *batch, const DevParams &p, u
         it = ctx->tune_table.emplace(key, choice).first;
         tune_save(ctx);
     }
-    if (!it->second.split) return AGATHA_OK;    // one launch measured faster
+    if (!it->second.split) {                    // one launch of one variant
+        const int v = it->second.var[0];
+        lp->lane16 = v != VAR_32;
+        lp->regs_high = v == VAR_16_HIGHREG;
+        return AGATHA_OK;
+    }
     lp->split = 1;
     for (int c = 0; c < N_CLASSES; ++c) lp->cls_var[c] = it->second.var[c];
     return AGATHA_OK;

@@ -72,6 +72,15 @@ def test_every_class_variant_is_exact(tmp_path, batch, reference, variants):
         assert A.results_equal(out.cpu().numpy().view(A.RESULT_DTYPE), reference).size == 0
 
 
+@pytest.mark.parametrize("variant", [1, 2])
+def test_single_launch_of_another_variant_is_exact(tmp_path, batch, reference, variant):
+    path = tmp_path / "tune.txt"
+    path.write_text(_key(batch.scoring, 16) + f" {variant} {variant} {variant} {variant} 0\n")
+    with A.Context(0, autotune=True, tune_cache_path=str(path)) as ctx:
+        assert ctx.tune_variants(batch.scoring) == [variant] * 4 + [0]
+        assert A.results_equal(A.agatha_align_batch(ctx, batch), reference).size == 0
+
+
 def test_split_launches_match_oracle_on_a_sample(tmp_path, batch, reference):
     path = tmp_path / "tune.txt"
     path.write_text(_key(batch.scoring, 16) + " 2 1 0 1 1\n")
