@@ -146,7 +146,8 @@ def _kernel_digest():
     for the build it was measured on."""
     import hashlib
     h = hashlib.sha256()
-    for f in ("kernel_warp16.cuh", "kernel_warp16_c16.cu", "agatha_dev.cuh"):
+    for f in ("kernel_warp16.cuh", "kernel_warp16_c8.cu", "kernel_warp16_c16.cu", "kernel_warp16_c24.cu",
+              "agatha_dev.cuh"):
         with open(os.path.join(ROOT, "paper_2403_06478_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
@@ -224,6 +225,8 @@ def main():
     ap.add_argument("--plain-steps", type=int, default=3)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-sample-pairs", type=int, default=CPU_SAMPLE_PAIRS)
+    ap.add_argument("--tune-cache", default=None,
+                    help="autotuner cache file: read if present, written after tuning")
     ap.add_argument("--workload", default="ont", choices=sorted(WORKLOADS),
                     help="ont (the headline), or another configuration of the same metric")
     args = ap.parse_args()
@@ -248,7 +251,7 @@ def main():
     batch = W.make_config(args.workload, seed=None if rank == 0 else W.SEED_BASE + 2 + 1000 * rank)
     pb = A.pack_batch(batch)
     n = pb.n_pairs
-    ctx = A.Context(local, timing=True, autotune=True)
+    ctx = A.Context(local, timing=True, autotune=True, tune_cache_path=args.tune_cache)
     # a dedicated stream: every launch, copy and timing event of the step sits on it
     stream = torch.cuda.Stream()
     torch.cuda.set_stream(stream)
@@ -342,7 +345,13 @@ def main():
     cells16 = int(res["cells"][lane16].sum())
     ops = cells16 * OPS_PER_CELL_I16X2 + (cells - cells16) * OPS_PER_CELL_I32
     achieved = ops / (k_ms / 1e3) / 1e12
-    kernel = "warp16_align_kernel<16, 4>" if cells16 * 2 > cells else "warp_align_kernel<16>"
+    # the kernel the (tuned) plan launches: slots per lane from the band, the
+    # resident blocks per SM from the register budget the tuner chose
+    w = batch.scoring.w
+    c16 = 8 if 0 < w <= 255 else (16 if 0 < w <= 511 else 24)
+    high = bool(tuned) and not tuned[4] and tuned[0] == 1
+    minb = (4 if c16 <= 16 else 3) - (1 if high else 0)
+    kernel = f"warp16_align_kernel<{c16}, {minb}>" if cells16 * 2 > cells else "warp_align_kernel"
     # kernels per step: prep classify/scan/scatter, the warp kernel (one per
     # length class when the autotuner split the queue) and, with 16-bit lanes,
     # the int32 kernel over the (usually empty) overflow list

@@ -82,6 +82,10 @@ __device__ __forceinline__ uint32_t mux(uint32_t m, uint32_t x, uint32_t y) {
 
 struct Cold16 {
     int32_t mqe, mqe_t, mte, mte_q, gscore;
+    int32_t gt, gq;               // cell of the global maximum
+    int32_t Dp, LOWCHK, kint;     // step bound, lowest allowed score, rebase interval
+    int32_t pad;
+    int64_t cells;
 };
 
 // DMREG: keep the dead-slot masks in registers (the larger register budget)
@@ -97,8 +101,11 @@ struct WarpPair16 {
     // slot p+P at bit 2p of hi (C = 24), or at bit 16+2p of lo (C <= 16)
     struct Comb { uint32_t lo, hi; };
 
+    // each sequence as its own words: base k of the pair at index k + phase
+    // of the words from tp (qp); reads outside [0, span) words give 0 (those
+    // bases only reach cells outside the table)
     const uint32_t *tp, *qp;
-    int64_t tw, qw, toff, qoff;
+    int32_t tspan, qspan;
     int32_t tlen, qlen, w, last_r, lane, j0;
     DevParams prm;
     int32_t oe, oe2;
@@ -116,20 +123,18 @@ struct WarpPair16 {
     Win Tw, Qw;
     uint32_t Tpf, Qpf;
     int32_t tcnt, qcnt;
-    int64_t tpos, qpos;
+    int32_t tpos, qpos;    // next prefetch position (bases, word-relative)
     // relative scores
-    int32_t base, Dp, LOWCHK, OFF, last_m;
+    int32_t base, OFF, last_m;
     int32_t until_rebase;  // anti-diagonals left before the next rebase
-    int32_t kint;          // the rebase interval K
     bool ovf;
     // packed constants
     uint32_t A2, NB2, OEp, DOEp, Ep, E2p, NEp, NE2p, NEGp, L0LO, L31HI;
     // bookkeeping (uniform across the warp)
-    int32_t gmax, gt, gq;
-    int64_t cells;
+    int32_t gmax;
     int32_t zdropped;
-    // results only the table edges change, kept in shared memory (written by
-    // lane 0) so they hold no registers through the bulk loop
+    // state the bulk step never reads, kept in shared memory (written by lane
+    // 0) so that it holds no registers through the bulk loop
     Cold16 &cold;
 
     __device__ explicit WarpPair16(Cold16 &c) : cold(c) {}
@@ -139,21 +144,34 @@ struct WarpPair16 {
     __device__ __forceinline__ int32_t frame(int32_t r) const { return floor_div2(r - w); }
 
     // ------------------------------------------------------------ windows
-    __device__ __forceinline__ void init_windows(int32_t r) {
+    // 16 bases from word-relative base index a (any a; outside the span: 0)
+    __device__ __forceinline__ static uint32_t load_rel(const uint32_t *__restrict__ p, int32_t span,
+                                                        int32_t a) {
+        const int32_t wi = a >> 4;                     // floor for negative a too
+        const uint32_t lo = (uint32_t)wi < (uint32_t)span ? __ldg(p + wi) : 0u;
+        const uint32_t hi = (uint32_t)(wi + 1) < (uint32_t)span ? __ldg(p + wi + 1) : 0u;
+        return __funnelshift_r(lo, hi, (uint32_t)(a & 15) * 2u);
+    }
+    __device__ __forceinline__ static uint64_t load_rel32(const uint32_t *__restrict__ p, int32_t span,
+                                                          int32_t a) {
+        return (uint64_t)load_rel(p, span, a) | ((uint64_t)load_rel(p, span, a + 16) << 32);
+    }
+    // tph/qph: the phase of the pair's first base in its first word
+    __device__ __forceinline__ void init_windows(int32_t r, int32_t tph, int32_t qph) {
         const int32_t B = frame(r);
-        const int64_t tb = (int64_t)B + j0;
-        const int64_t qb = (int64_t)r - B - j0;
+        const int32_t tb = B + j0 + tph;
+        const int32_t qb = r - B - j0 + qph;
         if constexpr (C <= 16) {
-            Tw = load16(tp, tw, toff + tb) & WMASK;
-            Qw = rev2_32(load16(qp, qw, qoff + qb - C + 1)) >> (2 * (16 - C));
+            Tw = load_rel(tp, tspan, tb) & WMASK;
+            Qw = rev2_32(load_rel(qp, qspan, qb - C + 1)) >> (2 * (16 - C));
         } else {
-            Tw = load32(tp, tw, toff + tb) & WMASK;
-            Qw = rev2_64(load32(qp, qw, qoff + qb - C + 1)) >> (2 * (32 - C));
+            Tw = load_rel32(tp, tspan, tb) & WMASK;
+            Qw = rev2_64(load_rel32(qp, qspan, qb - C + 1)) >> (2 * (32 - C));
         }
         tpos = tb + C;
         qpos = qb + 1;
-        Tpf = load16(tp, tw, toff + tpos);
-        Qpf = load16(qp, qw, qoff + qpos);
+        Tpf = load_rel(tp, tspan, tpos);
+        Qpf = load_rel(qp, qspan, qpos);
         tpos += 16;
         qpos += 16;
         tcnt = 16;
@@ -162,12 +180,12 @@ struct WarpPair16 {
     __device__ __forceinline__ void shift_t() {
         Tw = (Tw >> 2) | ((Win)(Tpf & 3u) << (2 * C - 2));
         Tpf >>= 2;
-        if (--tcnt == 0) { Tpf = load16(tp, tw, toff + tpos); tpos += 16; tcnt = 16; }
+        if (--tcnt == 0) { Tpf = load_rel(tp, tspan, tpos); tpos += 16; tcnt = 16; }
     }
     __device__ __forceinline__ void shift_q() {
         Qw = ((Qw << 2) | (Win)(Qpf & 3u)) & WMASK;
         Qpf >>= 2;
-        if (--qcnt == 0) { Qpf = load16(qp, qw, qoff + qpos); qpos += 16; qcnt = 16; }
+        if (--qcnt == 0) { Qpf = load_rel(qp, qspan, qpos); qpos += 16; qcnt = 16; }
     }
     // windows of anti-diagonal r from those of r-1
     __device__ __forceinline__ void advance(int32_t r) {
@@ -230,9 +248,12 @@ struct WarpPair16 {
     __device__ __forceinline__ bool max_and_zdrop(int32_t m, int32_t tstar, int32_t r) {
         const int32_t qstar = r - tstar;
         if (m > gmax) {
-            gmax = m; gt = tstar; gq = qstar;
+            gmax = m;
+            if (lane == 0) { cold.gt = tstar; cold.gq = qstar; }
+            __syncwarp();
             return false;
         }
+        const int32_t gt = cold.gt, gq = cold.gq;
         if (tstar >= gt && qstar >= gq && prm.zdrop >= 0) {
             int32_t l = (tstar - gt) - (qstar - gq);
             l = l < 0 ? -l : l;
@@ -317,7 +338,7 @@ struct WarpPair16 {
             if (r + 1 < qlen) vb |= slot_bit(-1 - B - j0);                 // (-1, r+1)
             if (r >= -1 && r + 1 < tlen) vb |= slot_bit(r + 1 - B - j0);  // (r+1, -1)
             const int32_t vv = to_u(r == -2 ? 0 : -gap_cost(prm, r + 2));
-            if (__any_sync(FULL, vb != 0u) && (vv < LOWCHK || vv > 0xffff - Dp)) ovf = true;
+            if (__any_sync(FULL, vb != 0u) && (vv < cold.LOWCHK || vv > 0xffff - cold.Dp)) ovf = true;
             VVp = (uint32_t)vv * 0x10001u;
             VVe = (uint32_t)(vv - oe) * 0x10001u;
             VVe2 = (uint32_t)(vv - oe2) * 0x10001u;
@@ -341,7 +362,7 @@ struct WarpPair16 {
                 const int32_t ts = frame(r - 1) + 32 * C, qs = r - 1 - ts;
                 if (qs == -1 && ts >= 0 && ts < tlen) {
                     const int32_t v = to_u(-gap_cost(prm, ts + 1));
-                    if (v < LOWCHK || v > 0xffff - Dp) ovf = true;
+                    if (v < cold.LOWCHK || v > 0xffff - cold.Dp) ovf = true;
                     inj = ((uint32_t)(v - oe) << 16) | (NEGp & 0xffffu);
                     inj2 = ((uint32_t)(v - oe2) << 16) | (NEGp & 0xffffu);
                 }
@@ -413,7 +434,7 @@ struct WarpPair16 {
         } else {
             if (__any_sync(FULL, ovf)) { ovf = true; return true; }
             if (r < 0) return false;
-            cells += en - st + 1;
+            if (lane == 0) cold.cells += en - st + 1;
             // best score on the last target row / the last query column
             bool set_gs = false;
             int32_t gs = K_NEG_OUT;
@@ -481,9 +502,9 @@ struct WarpPair16 {
     // reset like the slots beyond the band and not checked.
     __device__ __forceinline__ void rebase(int32_t m_u, int32_t r, uint32_t in_r = ~0u,
                                            uint32_t in_r1 = ~0u) {
-        until_rebase = kint;
+        until_rebase = cold.kint;
         const int32_t delta = m_u - OFF;
-        const int32_t low = min(max(LOWCHK - Dp + delta, 0), 0xffff);
+        const int32_t low = min(max(cold.LOWCHK - cold.Dp + delta, 0), 0xffff);
         const uint32_t low2 = (uint32_t)low * 0x10001u;
         const bool odd = ((r - w) & 1) != 0;
         const uint32_t in_ev = odd ? in_r1 : in_r, in_od = odd ? in_r : in_r1;
@@ -522,9 +543,19 @@ struct WarpPair16 {
     __device__ __forceinline__ bool run(const DevBatch &Bt, int32_t pair, int32_t lane_, bool use_fast) {
         prm = Bt.params;
         lane = lane_;
-        tp = Bt.t_packed; qp = Bt.q_packed; tw = Bt.t_words; qw = Bt.q_words;
         tlen = Bt.t_len[pair]; qlen = Bt.q_len[pair];
-        toff = Bt.t_off[pair]; qoff = Bt.q_off[pair];
+        int32_t tph, qph;
+        {
+            const int64_t toff = Bt.t_off[pair], qoff = Bt.q_off[pair];
+            const int64_t tw0 = toff >> 4, qw0 = qoff >> 4;
+            tp = Bt.t_packed + tw0;
+            qp = Bt.q_packed + qw0;
+            tph = (int32_t)(toff & 15);
+            qph = (int32_t)(qoff & 15);
+            // the words the pair's bases occupy (inside the stream: checked by prep)
+            tspan = (int32_t)min(Bt.t_words - tw0, (int64_t)((tph + tlen + 15) >> 4));
+            qspan = (int32_t)min(Bt.q_words - qw0, (int64_t)((qph + qlen + 15) >> 4));
+        }
         agatha_result *out = Bt.out + pair;
         if (tlen <= 0 || qlen <= 0) {
             if (lane == 0) write_empty_result(out);
@@ -534,11 +565,16 @@ struct WarpPair16 {
         oe = prm.q + prm.e; oe2 = prm.q2 + prm.e2;
         j0 = lane * C;
         last_r = tlen + qlen - 2;
-        Dp = step_change_max(prm);
-        kint = rebase_interval(Dp);
-        until_rebase = kint;
-        LOWCHK = (int32_t)U_NEG + (kint + 3) * Dp;
-        OFF = 0xffff - (kint + 3) * Dp;
+        {
+            const int32_t Dp = step_change_max(prm), kint = rebase_interval(Dp);
+            until_rebase = kint;
+            OFF = 0xffff - (kint + 3) * Dp;
+            if (lane == 0) {
+                cold.Dp = Dp;
+                cold.kint = kint;
+                cold.LOWCHK = (int32_t)U_NEG + (kint + 3) * Dp;
+            }
+        }
         base = 0;
         last_m = OFF;
         ovf = false;
@@ -566,16 +602,18 @@ struct WarpPair16 {
                     DMR[p] = prmt(DF2 - ((uint32_t)p | ((uint32_t)(p + P) << 16)), 0, 0xbb99);
             }
         }
-        gmax = 0; gt = -1; gq = -1;
+        gmax = 0;
         if (lane == 0) {
             cold.mqe = K_NEG_OUT; cold.mqe_t = -1; cold.mte = K_NEG_OUT; cold.mte_q = -1;
             cold.gscore = K_NEG_OUT;
+            cold.gt = -1; cold.gq = -1;
+            cold.cells = 0;
         }
         __syncwarp();
-        cells = 0; zdropped = 0;
+        zdropped = 0;
 
         int32_t r = -2;
-        init_windows(r);
+        init_windows(r, tph, qph);
         bool stop = head_step(r);
         const int32_t head_end = min(last_r, w + 1);
         while (!stop && r < head_end) {
@@ -601,7 +639,7 @@ struct WarpPair16 {
             // every bulk anti-diagonal holds the whole band: w + 1 cells when
             // (r - w) is even, w when it is odd; the first one is even
             const int32_t nb = r - r0;
-            cells += (int64_t)(nb >> 1) * (2 * w + 1) + (int64_t)(nb & 1) * (w + 1);
+            if (lane == 0) cold.cells += (int64_t)(nb >> 1) * (2 * w + 1) + (int64_t)(nb & 1) * (w + 1);
         }
         while (!stop && r < last_r) {     // r > w + 1 here
             ++r;
@@ -612,10 +650,10 @@ struct WarpPair16 {
         if (lane == 0) {
             agatha_result o;
             const int32_t mqe = cold.mqe;
-            o.max = gmax; o.te = gt; o.qe = gq;
+            o.max = gmax; o.te = cold.gt; o.qe = cold.gq;
             o.gscore = cold.gscore; o.mqe = mqe; o.mqe_t = cold.mqe_t; o.mte = cold.mte;
             o.mte_q = cold.mte_q;
-            o.cells = cells;
+            o.cells = cold.cells;
             o.zdropped = (uint8_t)zdropped;
             o.reach_end = (uint8_t)(!zdropped && mqe != K_NEG_OUT && mqe + prm.end_bonus > gmax);
             o.lane16 = 1;
