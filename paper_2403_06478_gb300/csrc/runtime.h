@@ -146,6 +146,7 @@ struct agatha_ctx {
     bool timed_once = false;
     cudaEvent_t ev_k0 = nullptr, ev_k1 = nullptr;
     bool autotune = false;             // AGATHA_CFG_AUTOTUNE
+    std::mutex tune_mu;                // guards tune_table (align_batch and the server read it)
     std::map<std::string, agatha::TuneChoice> tune_table;
     cudaEvent_t tune_ev0 = nullptr, tune_ev1 = nullptr;
 };

@@ -315,6 +315,7 @@ cudaError_t launch_slot(ServeState *S, ServeSlot *s, const DevParams &p, int32_t
         tb += (int64_t)r->t_words.size();
     }
     unsigned char *d = (unsigned char *)S->arena_base + s->block_off;
+    cudaStream_t st = s->stream;
 
     BatchShape shape;
     shape.n = n;
@@ -322,6 +323,8 @@ cudaError_t launch_slot(ServeState *S, ServeSlot *s, const DevParams &p, int32_t
     shape.max_w_warp = shape.max_w_all;
     LaunchPlan lp;
     if (make_plan(ctx, p, shape, 0, &lp) != AGATHA_OK) return cudaErrorInvalidValue;
+    // the plan the context's autotuner chose for this scoring, if any (no measuring here)
+    if (tune_apply(ctx, nullptr, p, AGATHA_DEVICE_PTRS, st, &lp) != AGATHA_OK) return cudaErrorInvalidValue;
 
     DevBatch *desc = s->slot.h_desc;
     desc->q_packed = (const uint32_t *)(d + L.q_packed);
@@ -336,7 +339,6 @@ cudaError_t launch_slot(ServeState *S, ServeSlot *s, const DevParams &p, int32_t
     desc->n_pairs = n;
     fill_desc(&s->slot, desc, p, lp, d + L.order, d + L.wide, d + L.ovf);
 
-    cudaStream_t st = s->stream;
     cudaError_t e = cudaMemcpyAsync(d, h, (size_t)L.in_end, cudaMemcpyHostToDevice, st);
     if (e == cudaSuccess) e = cudaMemcpyAsync(s->slot.d_desc, desc, sizeof(DevBatch), cudaMemcpyHostToDevice, st);
     if (e == cudaSuccess) e = slot_run(ctx, &s->slot, lp, st, nullptr, nullptr);

@@ -38,6 +38,7 @@ std::string tune_key(const agatha_ctx *ctx, const DevParams &p, int C16) {
     return buf;
 }
 
+// (ctx->tune_mu held)
 void tune_save(agatha_ctx *ctx) {
     if (ctx->tune_cache_path.empty()) return;
     const std::string tmp = ctx->tune_cache_path + ".tmp";
@@ -202,23 +203,31 @@ int tune_apply(agatha_ctx *ctx, const agatha_batch *batch, const DevParams &p, u
     const uint32_t off = AGATHA_NO_TUNE | AGATHA_PLAIN | AGATHA_FORCE32 | AGATHA_NO_SORT | AGATHA_REGS_HIGH;
     if (!ctx->autotune || (flags & off) || lp->plain || !lp->lane16 || !lp->sort) return AGATHA_OK;
     const std::string key = tune_key(ctx, p, lp->C16);
-    auto it = ctx->tune_table.find(key);
-    if (it == ctx->tune_table.end()) {
-        if (flags & AGATHA_DEVICE_PTRS) return AGATHA_OK;   // lengths on the device: default plan
-        TuneChoice choice;
+    TuneChoice choice;
+    bool found;
+    {
+        std::lock_guard<std::mutex> g(ctx->tune_mu);
+        auto it = ctx->tune_table.find(key);
+        found = it != ctx->tune_table.end();
+        if (found) choice = it->second;
+    }
+    if (!found) {
+        // lengths on the device (or a serving launch): the default plan
+        if ((flags & AGATHA_DEVICE_PTRS) || !batch) return AGATHA_OK;
         const int rc = tune_run(ctx, batch, p, flags, s, *lp, &choice);
         if (rc) return rc;
-        it = ctx->tune_table.emplace(key, choice).first;
+        std::lock_guard<std::mutex> g(ctx->tune_mu);
+        ctx->tune_table[key] = choice;
         tune_save(ctx);
     }
-    if (!it->second.split) {                    // one launch of one variant
-        const int v = it->second.var[0];
+    if (!choice.split) {                        // one launch of one variant
+        const int v = choice.var[0];
         lp->lane16 = v != VAR_32;
         lp->regs_high = v == VAR_16_HIGHREG;
         return AGATHA_OK;
     }
     lp->split = 1;
-    for (int c = 0; c < N_CLASSES; ++c) lp->cls_var[c] = it->second.var[c];
+    for (int c = 0; c < N_CLASSES; ++c) lp->cls_var[c] = choice.var[c];
     return AGATHA_OK;
 }
 
@@ -234,7 +243,7 @@ extern "C" int agatha_tune_variants(agatha_ctx *ctx, const agatha_params *params
     const int32_t w = w_max < 0 ? 32 * 32 - 1 : w_max;
     const int C16 = pick_slots16(w);
     if (C16 == 0 || step_change_max(p) > 64) return AGATHA_ENOTSUP;
-    std::lock_guard<std::mutex> lock(ctx->mu);
+    std::lock_guard<std::mutex> lock(ctx->tune_mu);
     auto it = ctx->tune_table.find(tune_key(ctx, p, C16));
     if (it == ctx->tune_table.end()) return AGATHA_EAGAIN;
     for (int c = 0; c < N_CLASSES; ++c) variants[c] = it->second.var[c];

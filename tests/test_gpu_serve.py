@@ -143,3 +143,19 @@ def test_empty_request_and_bad_input(ctx, pools):
         assert srv.poll(987654321) == A.AGATHA_EINVAL
     finally:
         srv.stop()
+
+
+def test_serving_uses_the_tuned_plan(tmp_path, ctx, pools):
+    import torch
+    prop = torch.cuda.get_device_properties(0)
+    s = pools["ont"].scoring
+    key = (f"sm{prop.multi_processor_count}_cc{prop.major}{prop.minor}_a{s.a}_b{s.b}_q{s.q}_e{s.e}"
+           f"_q2{s.q2}_e2{s.e2}_w{s.w}_z{s.zdrop}_c16")
+    path = tmp_path / "tune.txt"
+    path.write_text(key + " 2 1 0 1 1\n")           # one launch per class, mixed variants
+    reqs = [r for r in _requests(pools, 30, 13) if r.scoring == s]
+    with A.Context(0, autotune=True, tune_cache_path=str(path)) as tuned:
+        got, st = _serve_all(tuned, reqs, max_inflight=2, max_batch_pairs=400, linger_us=2000)
+    assert st["requests_done"] == len(reqs)
+    for b, g in zip(reqs, got):
+        assert A.results_equal(g, A.agatha_align_batch(ctx, b)).size == 0
