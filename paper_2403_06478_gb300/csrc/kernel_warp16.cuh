@@ -89,8 +89,12 @@ struct Cold16 {
 };
 
 // DMREG: keep the dead-slot masks in registers (the larger register budget)
-// instead of recomputing them at every use.
-template <int C, bool DMREG>
+// instead of recomputing them at every use.  DEFER: a new maximum found by a
+// bulk step is only located (its cell found) when that can matter: before the
+// next Z-drop test and when the bulk loop ends; until then the H values of its
+// anti-diagonal are kept, so a run of growing maxima costs one copy each
+// instead of one search each.
+template <int C, bool DMREG, bool DEFER = false>
 struct WarpPair16 {
     static_assert(C == 8 || C == 16 || C == 24, "16-bit lanes use 8, 16 or 24 slots per lane");
     static constexpr int P = C / 2;
@@ -118,6 +122,8 @@ struct WarpPair16 {
     // (k0 - 1) in both halves so that dead_mask() is one add and one prmt
     uint32_t DF2;
     uint32_t DMR[DMREG ? P : 1];   // DMREG: dead_mask(p), computed once per pair
+    uint32_t Hsave[DEFER ? P : 1]; // DEFER: H of the pending maximum's anti-diagonal
+    int32_t pend_r, pend_m, pend_lm;   // its anti-diagonal (-3: none), maximum, lane maximum
     // base windows (2 bits per slot): Tw field jl = T[B + j0 + jl],
     // Qw field jl = Q[r - B - j0 - jl]
     Win Tw, Qw;
@@ -266,13 +272,49 @@ struct WarpPair16 {
     // H - q - e over the lane's band cells (others 0); Hn: the H values of r;
     // excl(p): 0xFFFF halves of slots that are not band cells.  Returns true
     // to stop.
-    template <bool ODD, typename Excl>
+    // Locate a pending maximum (DEFER): the same search as anti_diagonal_max
+    // on the kept H values; sets the cell of the global maximum.
+    __device__ __forceinline__ void locate_pending() {
+        if constexpr (DEFER) {
+            if (pend_r == -3) return;
+            const unsigned ball = __ballot_sync(FULL, pend_lm == pend_m);
+            const int src = __ffs(ball) - 1;
+            const uint32_t mh2 = (uint32_t)(pend_m + oe) * 0x10001u;
+            const uint32_t x0 = ((pend_r - w) & 1) ? L0LO : 0u;   // slot 0 of lane 0 on odd ones
+            uint32_t ne = 0;
+#pragma unroll
+            for (int p = 0; p < P; ++p) ne += __vminu2((Hsave[p] ^ mh2) | (p == 0 ? x0 : 0u), 0x10001u) << p;
+            const uint32_t eq = ~ne & ((((1u << P) - 1) << 16) | ((1u << P) - 1));
+            const uint32_t lo_eq = eq & 0xffffu, hi_eq = eq >> 16;
+            const int32_t jl = lo_eq ? __ffs(lo_eq) - 1 : P + __ffs(hi_eq) - 1;
+            const int32_t lj = __shfl_sync(FULL, jl, src);
+            const int32_t tstar = frame(pend_r) + src * C + lj;
+            if (lane == 0) { cold.gt = tstar; cold.gq = pend_r - tstar; }
+            __syncwarp();
+            pend_r = -3;
+        }
+    }
+
+    template <bool ODD, typename Excl, bool BULKSTEP = false>
     __device__ __forceinline__ bool anti_diagonal_max(int32_t r, int32_t B, uint32_t lmax,
                                                       const uint32_t (&Hn)[P], Excl excl) {
         const int32_t lm = (int32_t)max(lmax & 0xffffu, lmax >> 16);
         const int32_t m = __reduce_max_sync(FULL, lm);
         const int32_t mt = to_true(m + oe);
         last_m = m + oe;
+        if constexpr (DEFER && BULKSTEP) {
+            if (mt > gmax) {                   // keep it; locate it when needed
+                gmax = mt;
+#pragma unroll
+                for (int p = 0; p < P; ++p) Hsave[p] = Hn[p];
+                pend_r = r;
+                pend_m = m;
+                pend_lm = lm;
+                return false;
+            }
+            if (!(prm.zdrop >= 0 && gmax - mt > prm.zdrop)) return false;
+            locate_pending();
+        }
         if (mt > gmax || (prm.zdrop >= 0 && gmax - mt > prm.zdrop)) {
             // position only when it can matter: lowest slot of the first lane
             // holding the maximum; bit p / 16+p of `ne` is set where the low /
@@ -429,8 +471,8 @@ struct WarpPair16 {
             // slots beyond the band sit above every band slot of their lane, so
             // the lowest slot holding the maximum is a band slot; only slot 0 of
             // lane 0 (below the band on odd anti-diagonals) is excluded
-            return anti_diagonal_max<ODD>(r, B, lmax, Hd,
-                                          [&](int p) { return (ODD && p == 0) ? L0LO : 0u; });
+            auto excl = [&](int p) { return (ODD && p == 0) ? L0LO : 0u; };
+            return anti_diagonal_max<ODD, decltype(excl), true>(r, B, lmax, Hd, excl);
         } else {
             if (__any_sync(FULL, ovf)) { ovf = true; return true; }
             if (r < 0) return false;
@@ -603,6 +645,7 @@ struct WarpPair16 {
             }
         }
         gmax = 0;
+        pend_r = -3;
         if (lane == 0) {
             cold.mqe = K_NEG_OUT; cold.mqe_t = -1; cold.mte = K_NEG_OUT; cold.mte_q = -1;
             cold.gscore = K_NEG_OUT;
@@ -636,6 +679,7 @@ struct WarpPair16 {
                 }
                 r += 2;
             }
+            locate_pending();
             // every bulk anti-diagonal holds the whole band: w + 1 cells when
             // (r - w) is even, w when it is odd; the first one is even
             const int32_t nb = r - r0;
@@ -678,7 +722,7 @@ warp16_align_kernel(const DevBatch *__restrict__ d_batch, int32_t use_fast, int3
         if (k >= L.end) break;
         const int32_t pair = L.items ? L.items[k] : k;
         if (!L.items && (!pair_valid(B, pair) || !warp_takes(B, pair))) continue;
-        WarpPair16<C, (MINB < 4 && C <= 16)> wp(cold[threadIdx.x >> 5]);
+        WarpPair16<C, (MINB < 4 && C <= 16), (MINB < 4 && C <= 16)> wp(cold[threadIdx.x >> 5]);
         if (!wp.run(B, pair, lane, use_fast != 0) && lane == 0) {
             const int32_t slot = atomicAdd(&B.counters[CTR_NOVF], 1);
             B.ovf_list[slot] = pair;
