@@ -189,10 +189,10 @@ int64_t agatha_band_cells(int32_t tlen, int32_t qlen, int32_t w);
  * four length classes by predicted band cells (the Section 4.5 model:
  * >= 2^25, >= 2^23, >= 2^21, smaller; up to 4096 pairs each) is timed with
  * each variant (0: 16-bit lanes, 1: 16-bit lanes at the larger register
- * budget, 2: int32 lanes).  If a class prefers another variant, the batch
- * (up to 131072 of its pairs) is timed as one launch of each winning variant
- * and, if the classes disagree, with one launch per class.  The fastest plan
- * is kept (anything but one launch of variant 0 must win by 3%), per context
+ * budget, 2: int32 lanes).  The batch (up to 131072 of its pairs) is then
+ * timed as one launch of each 16-bit variant (and of int32 lanes if a class
+ * preferred them) and, if the classes disagree, with one launch per class.  The fastest plan
+ * is kept (anything but one launch of variant 0 must win by 2%), per context
  * and in tune_cache_path (one line per key, read at agatha_init).  Every
  * variant gives bit-identical results.  agatha_tune_variants writes what was
  * tuned for `params` (band half-width w_max: the widest effective band of

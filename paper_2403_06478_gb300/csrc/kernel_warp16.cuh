@@ -722,7 +722,7 @@ warp16_align_kernel(const DevBatch *__restrict__ d_batch, int32_t use_fast, int3
         if (k >= L.end) break;
         const int32_t pair = L.items ? L.items[k] : k;
         if (!L.items && (!pair_valid(B, pair) || !warp_takes(B, pair))) continue;
-        WarpPair16<C, (MINB < 4 && C <= 16), (MINB < 4 && C <= 16)> wp(cold[threadIdx.x >> 5]);
+        WarpPair16<C, (MINB < 4 && C <= 16), true> wp(cold[threadIdx.x >> 5]);
         if (!wp.run(B, pair, lane, use_fast != 0) && lane == 0) {
             const int32_t slot = atomicAdd(&B.counters[CTR_NOVF], 1);
             B.ovf_list[slot] = pair;

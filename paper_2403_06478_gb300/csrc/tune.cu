@@ -7,11 +7,11 @@
 // chosen per length class, by measurement, the first time a host batch
 // arrives for a scoring and band width: the pairs of each class (up to 4096,
 // spread over the class) are aligned with every variant and the fastest one
-// kept (a variant other than the default must win by 3%).  If any class
-// prefers another variant, the batch itself (up to 131072 of its pairs) is
-// timed as one launch of each winning variant and, if the classes disagree,
-// as one launch per class; the fastest plan is kept (again with a 3% margin
-// for anything but one launch of the default variant).
+// kept (a variant other than the default must win by 2%).  The batch itself
+// (up to 131072 of its pairs) is then timed as one launch of each 16-bit
+// variant (and of int32 lanes if a class preferred them) and, if the classes
+// disagree, as one launch per class; the fastest plan is kept (again with a
+// 2% margin for anything but one launch of the default variant).
 // Every variant computes the same exact results, so the choice only moves
 // time.  Choices are kept per context and, with a cache path, in a text file
 // (one line per key: the key, the four class variants and the split flag).
@@ -101,7 +101,7 @@ struct SubBatch {
 };
 
 // A variant other than the default must win by this much to be taken.
-constexpr float kMargin = 0.97f;
+constexpr float kMargin = 0.98f;
 
 int tune_run(agatha_ctx *ctx, const agatha_batch *b, const DevParams &p, uint32_t flags, cudaStream_t s,
              const LaunchPlan &lp, TuneChoice *choice) {
@@ -141,10 +141,11 @@ int tune_run(agatha_ctx *ctx, const agatha_batch *b, const DevParams &p, uint32_
     }
     choice->split = 0;
     for (int c = 0; c < N_CLASSES; ++c) choice->var[c] = VAR_16;
-    if (!wins[VAR_16_HIGHREG] && !wins[VAR_32]) return AGATHA_OK;   // the default everywhere
-    // 2. the batch itself (up to kTuneSplitPairs of it) as one launch of the
-    //    default and of every variant that won a class, and as one launch per
-    //    class; the fastest plan is kept
+    // 2. the batch itself (up to kTuneSplitPairs of it) as one launch of each
+    //    16-bit variant (samples of a class can hide a few percent that the
+    //    whole batch shows) and of int32 lanes if a class preferred them, and
+    //    as one launch per class; the fastest plan is kept
+    wins[VAR_16_HIGHREG] = true;
     SubBatch whole(b, all, kTuneSplitPairs);
     float best = 0.f;
     int best_v = VAR_16;
