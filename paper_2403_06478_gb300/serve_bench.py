@@ -89,13 +89,19 @@ def main(argv=None):
     B.build()
     pool = W.make_config("ont")
     pool_pb = A.pack_batch(pool)
-    ctx = A.Context(args.device)
+    ctx = A.Context(args.device, autotune=True)
+    # the autotuner measures its plan on one host batch of the scoring; the
+    # server's merged launches then use it
+    ctx.align_host(pool_pb, pool.scoring)
+    tuned = ctx.tune_variants(pool.scoring)
     rng = np.random.default_rng(W.SEED_BASE + 5)
     for rate in [float(x) for x in args.rates.split(",")]:
         line = _point(ctx, pool_pb, pool, rate, args, rng)
         line["config"] = {"workload": "serving: Poisson arrivals, 1-512 ONT-like pairs per request",
                           "budget_gb": args.budget_gb, "max_inflight": args.max_inflight,
-                          "max_batch_pairs": args.max_batch_pairs, "linger_us": args.linger_us}
+                          "max_batch_pairs": args.max_batch_pairs, "linger_us": args.linger_us,
+                          "tuned_plan": None if tuned is None else
+                          {"variants": [A.VARIANT_NAMES[v] for v in tuned[:4]], "split": bool(tuned[4])}}
         print(json.dumps(line), flush=True)
     ctx.close()
 
