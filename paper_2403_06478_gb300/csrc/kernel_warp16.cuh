@@ -367,7 +367,7 @@ struct WarpPair16 {
         uint32_t (&Hd)[P] = ODD ? Hod : Hev;
         const int32_t B = frame(r);
         int32_t st = 0, en = -1;
-        uint32_t rb = 0, vb = 0, VVp = 0, VVe = 0, VVe2 = 0;
+        uint32_t rb = 0, vb = 0, VVp = 0;
         if constexpr (MODE != BULK) {
             if (r >= 0) {
                 st = max(max(0, r - qlen + 1), ceil_div2(r - w));
@@ -382,8 +382,6 @@ struct WarpPair16 {
             const int32_t vv = to_u(r == -2 ? 0 : -gap_cost(prm, r + 2));
             if (__any_sync(FULL, vb != 0u) && (vv < cold.LOWCHK || vv > 0xffff - cold.Dp)) ovf = true;
             VVp = (uint32_t)vv * 0x10001u;
-            VVe = (uint32_t)(vv - oe) * 0x10001u;
-            VVe2 = (uint32_t)(vv - oe2) * 0x10001u;
         }
         uint32_t edge, edge2;
         if constexpr (ODD) {
@@ -448,17 +446,23 @@ struct WarpPair16 {
                 Hd[p] = H;
                 mx = MODE == BULK ? hoe : (half_mask_rt(rb, p) & hoe);
             } else {
-                const uint32_t hoe = H - OEp;
-                const uint32_t hoe2 = hoe - DOEp;
+                // H of the band cells; the virtual row/column cell gets its
+                // exact value and every other slot minus infinity.  The gap
+                // states then follow from this H: a virtual cell's inputs come
+                // from slots at minus infinity, so it emits exactly
+                // -gap(r+2) - q - e (- q2 - e2); the other slots off the table
+                // emit at most NEG, or, past the table's end, values that only
+                // reach cells past the end
                 const uint32_t rm = half_mask_rt(rb, p);
                 const uint32_t vm = half_mask_rt(vb, p);
-                const uint32_t fillE = mux(vm, VVe, NEGp);
-                const uint32_t fillE2 = mux(vm, VVe2, NEGp);
-                Eo[p] = mux(rm, __viaddmax_u16x2(Ein, NEp, hoe), fillE);
-                Fo[p] = mux(rm, __viaddmax_u16x2(Fin, NEp, hoe), fillE);
-                E2o[p] = mux(rm, __viaddmax_u16x2(E2in, NE2p, hoe2), fillE2);
-                F2o[p] = mux(rm, __viaddmax_u16x2(F2in, NE2p, hoe2), fillE2);
-                Hd[p] = mux(rm, H, mux(vm, VVp, NEGp));
+                const uint32_t Hm = mux(rm, H, mux(vm, VVp, NEGp));
+                const uint32_t hoe = Hm - OEp;
+                const uint32_t hoe2 = hoe - DOEp;
+                Eo[p] = __viaddmax_u16x2(Ein, NEp, hoe);
+                Fo[p] = __viaddmax_u16x2(Fin, NEp, hoe);
+                E2o[p] = __viaddmax_u16x2(E2in, NE2p, hoe2);
+                F2o[p] = __viaddmax_u16x2(F2in, NE2p, hoe2);
+                Hd[p] = Hm;
                 mx = rm & hoe;
             }
             // running maximum, two registers per 3-input max
@@ -494,8 +498,10 @@ struct WarpPair16 {
                 return true;
             if (set_gs && lane == 0) cold.gscore = gs;
             if (--until_rebase <= 2) {
+                // slots off the table (past its end, or holding NEG) are
+                // reset; the virtual cells' values are kept
                 if (MODE == TAIL) rebase(last_m, r, rb, table_bits(r - 1));
-                else rebase(last_m, r);      // head: slots off the table hold NEG already
+                else rebase(last_m, r, rb | vb, table_bits(r - 1) | virtual_bits(r - 1));
             }
             return ovf;
         }
@@ -571,6 +577,14 @@ struct WarpPair16 {
             rebase_reg<SUB>(Fo[p], dm_r, d2, low2);
             rebase_reg<SUB>(F2o[p], dm_r, d2, low2);
         }
+    }
+    // lane bits of the virtual row/column cells among the slots of anti-diagonal r
+    __device__ __forceinline__ uint32_t virtual_bits(int32_t r) const {
+        const int32_t B = frame(r);
+        uint32_t vb = 0;
+        if (r + 1 < qlen) vb |= slot_bit(-1 - B - j0);
+        if (r >= -1 && r + 1 < tlen) vb |= slot_bit(r + 1 - B - j0);
+        return vb;
     }
     // lane bits of the table's cells among the slots of anti-diagonal r
     __device__ __forceinline__ uint32_t table_bits(int32_t r) const {
