@@ -146,8 +146,8 @@ def _kernel_digest():
     for the build it was measured on."""
     import hashlib
     h = hashlib.sha256()
-    for f in ("kernel_warp16.cuh", "kernel_warp16_c8.cu", "kernel_warp16_c16.cu", "kernel_warp16_c24.cu",
-              "agatha_dev.cuh"):
+    for f in ("kernel_warp16.cuh", "kernel_warp16_c4.cu", "kernel_warp16_c8.cu", "kernel_warp16_c16.cu",
+              "kernel_warp16_c24.cu", "agatha_dev.cuh"):
         with open(os.path.join(ROOT, "paper_2403_06478_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
@@ -348,9 +348,9 @@ def main():
     # the kernel the (tuned) plan launches: slots per lane from the band, the
     # resident blocks per SM from the register budget the tuner chose
     w = batch.scoring.w
-    c16 = 8 if 0 < w <= 255 else (16 if 0 < w <= 511 else 24)
+    c16 = 4 if 0 < w <= 127 else (8 if 0 < w <= 255 else (16 if 0 < w <= 511 else 24))
     high = bool(tuned) and not tuned[4] and tuned[0] == 1
-    minb = (4 if c16 <= 16 else 3) - (1 if high else 0)
+    minb = {4: (6, 4), 8: (4, 3), 16: (4, 3), 24: (3, 2)}[c16][1 if high else 0]
     kernel = f"warp16_align_kernel<{c16}, {minb}>" if cells16 * 2 > cells else "warp_align_kernel"
     # kernels per step: prep classify/scan/scatter, the warp kernel (one per
     # length class when the autotuner split the queue) and, with 16-bit lanes,

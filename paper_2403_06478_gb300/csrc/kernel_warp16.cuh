@@ -96,7 +96,7 @@ struct Cold16 {
 // instead of one search each.
 template <int C, bool DMREG, bool DEFER = false>
 struct WarpPair16 {
-    static_assert(C == 8 || C == 16 || C == 24, "16-bit lanes use 8, 16 or 24 slots per lane");
+    static_assert(C == 4 || C == 8 || C == 16 || C == 24, "16-bit lanes use 4, 8, 16 or 24 slots per lane");
     static constexpr int P = C / 2;
     // a base window holds 2 bits per slot
     using Win = typename std::conditional<(2 * C > 32), uint64_t, uint32_t>::type;
@@ -202,6 +202,7 @@ struct WarpPair16 {
         const Win nm = (x | (x >> 1)) & (Win)0x5555555555555555ull;    // slot jl at bit 2*jl
         if constexpr (C == 16) return {(uint32_t)nm, 0u};
         else if constexpr (C == 8) return {((uint32_t)nm & 0xffu) | (((uint32_t)nm & 0xff00u) << 8), 0u};
+        else if constexpr (C == 4) return {((uint32_t)nm & 0xfu) | (((uint32_t)nm & 0xf0u) << 12), 0u};
         else return {(uint32_t)(nm & 0xffffffu), (uint32_t)(nm >> 24)};
     }
     // 0xFFFF halves of register p where the slot's bases differ
@@ -736,7 +737,7 @@ warp16_align_kernel(const DevBatch *__restrict__ d_batch, int32_t use_fast, int3
         if (k >= L.end) break;
         const int32_t pair = L.items ? L.items[k] : k;
         if (!L.items && (!pair_valid(B, pair) || !warp_takes(B, pair))) continue;
-        WarpPair16<C, (MINB < 4 && C <= 16), true> wp(cold[threadIdx.x >> 5]);
+        WarpPair16<C, (MINB < 4 && C <= 16) || MINB < 3, true> wp(cold[threadIdx.x >> 5]);
         if (!wp.run(B, pair, lane, use_fast != 0) && lane == 0) {
             const int32_t slot = atomicAdd(&B.counters[CTR_NOVF], 1);
             B.ovf_list[slot] = pair;

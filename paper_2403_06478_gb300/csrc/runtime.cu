@@ -167,6 +167,8 @@ static cudaError_t launch_warp(int C, const DevBatch *d, int blocks, cudaStream_
 static cudaError_t launch_warp16(int C, int high, const DevBatch *d, int blocks, cudaStream_t s,
                                  int fast, int list) {
     switch (C * 2 + high) {
+        case 8: return launch_warp16_c<4, 6>(d, blocks, s, fast, list);
+        case 9: return launch_warp16_c<4, 4>(d, blocks, s, fast, list);
         case 16: return launch_warp16_c<8, 4>(d, blocks, s, fast, list);
         case 17: return launch_warp16_c<8, 3>(d, blocks, s, fast, list);
         case 32: return launch_warp16_c<16, 4>(d, blocks, s, fast, list);
@@ -178,6 +180,8 @@ static cudaError_t launch_warp16(int C, int high, const DevBatch *d, int blocks,
 
 int warp16_occupancy(int C, int high) {
     switch (C * 2 + high) {
+        case 8: return occupancy_warp16_c<4, 6>();
+        case 9: return occupancy_warp16_c<4, 4>();
         case 16: return occupancy_warp16_c<8, 4>();
         case 17: return occupancy_warp16_c<8, 3>();
         case 32: return occupancy_warp16_c<16, 4>();
@@ -189,6 +193,7 @@ int warp16_occupancy(int C, int high) {
 
 // Slots per lane of the 16-bit kernel for a band of half-width w (0: none).
 int pick_slots16(int32_t w) {
+    if (w <= 32 * 4 - 1) return 4;
     if (w <= 32 * 8 - 1) return 8;
     if (w <= 32 * 16 - 1) return 16;
     if (w <= 32 * 24 - 1) return 24;
