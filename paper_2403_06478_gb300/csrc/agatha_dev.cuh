@@ -97,7 +97,8 @@ __host__ __device__ inline int32_t effective_w(int32_t w, int32_t tlen, int32_t 
 }
 
 // The largest change of a score from one anti-diagonal to the next: the
-// 16-bit lanes are sized from it.
+// 16-bit lanes are sized from it and take it up to STEP16_MAX.
+constexpr int32_t STEP16_MAX = 255;
 __host__ __device__ inline int32_t step_change_max(const DevParams &p) {
     int32_t d = p.a > p.b ? p.a : p.b;
     d = d > p.q + p.e ? d : p.q + p.e;

@@ -404,9 +404,10 @@ int make_plan(agatha_ctx *ctx, const DevParams &p, const BatchShape &shape, uint
     const int occ = warp_occupancy(lp->C);
     lp->warp_blocks = ctx->n_sm * occ;
     // 16-bit packed lanes when the band fits and one anti-diagonal changes a
-    // score by at most 64 (the headroom the 16-bit kernel's rebasing keeps)
+    // score by at most 255 (the 16-bit kernel then still rebases at least
+    // every 50 anti-diagonals)
     lp->C16 = pick_slots16(shape.max_w_all);
-    lp->lane16 = !(flags & AGATHA_FORCE32) && lp->C16 > 0 && step_change_max(p) <= 64 && !lp->wide_w;
+    lp->lane16 = !(flags & AGATHA_FORCE32) && lp->C16 > 0 && step_change_max(p) <= STEP16_MAX && !lp->wide_w;
     lp->regs_high = (flags & AGATHA_REGS_HIGH) ? 1 : 0;
     lp->split = 0;
     if (lp->lane16) {

@@ -243,7 +243,7 @@ extern "C" int agatha_tune_variants(agatha_ctx *ctx, const agatha_params *params
     if (normalise_params(params, &p)) return AGATHA_EINVAL;
     const int32_t w = w_max < 0 ? 32 * 32 - 1 : w_max;
     const int C16 = pick_slots16(w);
-    if (C16 == 0 || step_change_max(p) > 64) return AGATHA_ENOTSUP;
+    if (C16 == 0 || step_change_max(p) > STEP16_MAX) return AGATHA_ENOTSUP;
     std::lock_guard<std::mutex> lock(ctx->tune_mu);
     auto it = ctx->tune_table.find(tune_key(ctx, p, C16));
     if (it == ctx->tune_table.end()) return AGATHA_EAGAIN;

@@ -111,6 +111,36 @@ def test_16bit_lanes_used_and_exact(ctx, name):
     assert A.results_equal(got, ref).size == 0
 
 
+@pytest.mark.parametrize("scoring", [
+    W.Scoring(1, 20, 4, 30, 4, 30, 511, -1, 0),     # steep single-piece gaps, no Z-drop
+    W.Scoring(2, 30, 33, 31, 33, 31, 767, -1, 0),   # the largest step the 16-bit lanes take
+    W.Scoring(1, 9, 16, 3, 41, 1, 300, -1, 0),      # assembly-like two-piece
+    W.Scoring(1, 19, 39, 3, 81, 1, 200, -1, 0),     # step bound 82 (> 64)
+    W.Scoring(10, 90, 100, 50, 200, 20, 127, 5000, 0),   # step bound 220, 4 slots per lane
+])
+def test_16bit_lanes_with_steep_penalties(ctx, scoring):
+    # far past the table's end (the band's last w anti-diagonals) and before
+    # its start, cells off the table fall by the full gap cost per base; they
+    # must stay clear of the cells of the table sharing their registers
+    rng = np.random.default_rng(23)
+    qs, ts = [], []
+    for L in (300, 700, 1200, 2500):
+        for k in range(6):
+            x = rng.integers(0, 4, L).astype(np.uint8)
+            y = x.copy()
+            y[rng.integers(0, L, L // 30)] = rng.integers(0, 4, L // 30)
+            cut = int(rng.integers(0, min(scoring.w, L // 2)))
+            qs.append(x)
+            ts.append(y[: L - cut] if k % 2 else np.concatenate([y, rng.integers(0, 4, cut)]).astype(np.uint8))
+    batch = W.from_pairs(qs, ts, scoring)
+    ref = O.align_batch(batch)
+    for path in ("batched", "edge_only", "regs_high"):
+        got = A.agatha_align_batch(ctx, batch, flags=PATHS[path])
+        _assert_same(got, ref, batch, f"steep/{path}")
+    got = A.agatha_align_batch(ctx, batch)
+    assert got["lane16"].mean() > 0.5
+
+
 def test_16bit_overflow_hands_pairs_to_int32(ctx):
     # identical sequences with a = b = 64 and a 1 + 63 l gap cost: on every
     # anti-diagonal the band edge sits about 32*511 + gap(511) = 48.5k below the
