@@ -273,6 +273,21 @@ def make_skewed(n_pairs: int = 100_000, seed: Optional[int] = None) -> Batch:
     return _build("skewed", rng, ql, em, SKEWED_SCORING)
 
 
+def make_long_ratio(long_frac: float, n_pairs: int = 20_000, long_len: int = 4096,
+                    short_len: int = 128, seed: Optional[int] = None) -> Batch:
+    """Two-length mix for the load-balancing study (the paper's synthetic
+    4096 bp / 128 bp experiment, Section 5.6): a fraction `long_frac` of the
+    pairs are long, shuffled among the short ones; small-config errors and
+    ONT-like scoring."""
+    rng = np.random.default_rng(SEED_BASE + 6 if seed is None else seed)
+    n_long = int(round(long_frac * n_pairs))
+    ql = np.full(n_pairs, short_len, dtype=np.int32)
+    ql[:n_long] = long_len
+    rng.shuffle(ql)
+    em = ErrorModel(sub=0.05, ins=0.025, dele=0.025)
+    return _build(f"long_ratio_{long_frac:g}", rng, ql, em, ONT_SCORING)
+
+
 def make_config(name: str, n_pairs: Optional[int] = None,
                 seed: Optional[int] = None) -> Batch:
     """Workload by name; ``n_pairs`` shrinks it (same distribution)."""
