@@ -7,6 +7,7 @@ statically so the library only needs the driver at run time.
 from __future__ import annotations
 
 import concurrent.futures as cf
+import fcntl
 import hashlib
 import os
 import shutil
@@ -63,8 +64,18 @@ def _compile(src: str, verbose: bool) -> str:
 
 
 def build(force: bool = False, verbose: bool = False) -> str:
-    """Compile and link the library; skipped when the sources are unchanged."""
+    """Compile and link the library; skipped when the sources are unchanged.
+    Concurrent callers (one process per GPU) wait for each other."""
     os.makedirs(BUILD_DIR, exist_ok=True)
+    with open(os.path.join(BUILD_DIR, "lock"), "w") as lock:
+        fcntl.flock(lock, fcntl.LOCK_EX)
+        try:
+            return _build_locked(force, verbose)
+        finally:
+            fcntl.flock(lock, fcntl.LOCK_UN)
+
+
+def _build_locked(force: bool, verbose: bool) -> str:
     stamp = os.path.join(BUILD_DIR, "stamp")
     digest = _inputs_digest()
     if not force and os.path.exists(LIB) and os.path.exists(stamp):
