@@ -18,6 +18,9 @@
  *     maximum the global maximum moves there; otherwise, if it lies below and
  *     to the right of the global maximum and the drop exceeds
  *     Z + e2*|(i-i')-(j-j')|, the extension stops.
+ *   - After the score path, the traceback (CIGAR) of one extension: the
+ *     edit operations of a best path to its end cell, under a stated tie
+ *     rule (orc_traceback_pair, at the end of this file).
  * Readings where the paper is silent (boundary, tie-breaks, outputs) follow the
  * minimap2 extension convention and are listed in the design notes.
  *
@@ -244,3 +247,146 @@ int orc_align_batch(const uint8_t *q_codes, const uint8_t *t_codes,
 }
 
 int orc_result_size(void) { return (int)sizeof(orc_result); }
+
+/* ----------------------------------------------------------------------- */
+/*
+ * Traceback of one extension: the edit operations of a best-scoring path from
+ * the origin (-1,-1) to a chosen end cell (end_t, end_q).  The paper reports
+ * scores only; the traceback is the step a mapper runs next on the same table.
+ * The rule (this implementation's reading, stated once here and in the
+ * design notes):
+ *   - H(t,q) was reached from the first of, in this order, the diagonal
+ *     H(t-1,q-1)+S, E, F, E2, F2 whose value equals H(t,q) (Eq. 1);
+ *   - a gap state E(t,q) (likewise F, E2, F2; Eq. 2-3 and the second piece)
+ *     extended the same state of its predecessor only when that was strictly
+ *     better than opening from the predecessor's H; on a tie it opened.
+ *   - The virtual first row and column are leading gaps: reaching (-1, q)
+ *     adds q+1 insertions, reaching (t, -1) adds t+1 deletions.
+ * Operations: M (diagonal, match or mismatch) consumes one base of each
+ * sequence, I (F states) one query base, D (E states) one target base.  They
+ * are returned run-length encoded from the start of the extension, as
+ * (length << 4) | op with op M=0, I=1, D=2.
+ *
+ * The table is filled row by row (t outer, q inner) over t <= end_t,
+ * q <= end_q inside the band, from the same recurrences as orc_align_pair;
+ * cells beyond the end cell cannot lie on a path to it.
+ *
+ * Returns the number of runs, or -1 (end cell outside the table or band,
+ * allocation failure, or more than `cap` runs).  *score_out receives
+ * H(end_t, end_q) (0 for an empty path: end_t < 0 or end_q < 0).
+ */
+#define ORC_OP_M 0u
+#define ORC_OP_I 1u
+#define ORC_OP_D 2u
+
+typedef struct { uint32_t *ops; int64_t n, cap; uint32_t op, len; } orc_runs;
+
+/* Prepend (the walk goes backwards) `len` operations `op`. */
+static void orc_push(orc_runs *r, uint32_t op, uint32_t len)
+{
+    if (len == 0) return;
+    if (r->len > 0 && r->op == op) { r->len += len; return; }
+    if (r->len > 0) {
+        if (r->n < r->cap) r->ops[r->n] = (r->len << 4) | r->op;
+        r->n++;
+    }
+    r->op = op; r->len = len;
+}
+
+int64_t orc_traceback_pair(const uint8_t *T, int32_t tlen, const uint8_t *Q, int32_t qlen,
+                           const orc_params *p_in, int32_t end_t, int32_t end_q,
+                           uint32_t *ops, int64_t cap, int64_t *score_out)
+{
+    orc_params p = *p_in;
+    *score_out = 0;
+    if (end_t < 0 || end_q < 0) return 0;
+    if (end_t >= tlen || end_q >= qlen) return -1;
+    int64_t w = p.w;
+    if (w < 0 || w > (int64_t)(tlen > qlen ? tlen : qlen)) w = tlen > qlen ? tlen : qlen;
+    if (!in_band(end_t, end_q, tlen, qlen, w)) return -1;
+
+    const int64_t nt = (int64_t)end_t + 1, nq = (int64_t)end_q + 1, bw = 2 * w + 1;
+    /* per band cell: bits 0-2 the source of H (0 diagonal, 1 E, 2 F, 3 E2,
+       4 F2); bits 3-6 whether E, F, E2, F2 of this cell extended */
+    uint8_t *dir = (uint8_t *)calloc((size_t)(nt * bw), 1);
+    cell_state *row_prev = (cell_state *)malloc(sizeof(cell_state) * (size_t)nq);
+    cell_state *row_cur = (cell_state *)malloc(sizeof(cell_state) * (size_t)nq);
+    if (!dir || !row_prev || !row_cur) { free(dir); free(row_prev); free(row_cur); return -1; }
+
+    for (int64_t t = 0; t < nt; ++t) {
+        for (int64_t q = 0; q < nq; ++q) {
+            cell_state *c = &row_cur[q];
+            if (!in_band(t, q, tlen, qlen, w)) {
+                c->H = c->E = c->F = c->E2 = c->F2 = ORC_MINUS_INF;
+                continue;
+            }
+            /* predecessors, with the virtual row/column of Section 2.1's
+               extension boundary and minus infinity outside the band */
+            int64_t Hdiag;
+            if (t == 0 && q == 0) Hdiag = 0;
+            else if (t == 0) Hdiag = -gap_cost(&p, q);
+            else if (q == 0) Hdiag = -gap_cost(&p, t);
+            else Hdiag = row_prev[q - 1].H;
+            int64_t Hup, Eup, E2up, Hleft, Fleft, F2left;
+            if (t == 0) { Hup = -gap_cost(&p, q + 1); Eup = E2up = ORC_MINUS_INF; }
+            else { Hup = row_prev[q].H; Eup = row_prev[q].E; E2up = row_prev[q].E2; }
+            if (q == 0) { Hleft = -gap_cost(&p, t + 1); Fleft = F2left = ORC_MINUS_INF; }
+            else { Hleft = row_cur[q - 1].H; Fleft = row_cur[q - 1].F; F2left = row_cur[q - 1].F2; }
+
+            uint8_t d = 0;
+            int64_t open = Hup - p.q - p.e, ext = Eup - p.e;
+            c->E = ext > open ? ext : open;     if (ext > open) d |= 8;
+            open = Hleft - p.q - p.e; ext = Fleft - p.e;
+            c->F = ext > open ? ext : open;     if (ext > open) d |= 16;
+            open = Hup - p.q2 - p.e2; ext = E2up - p.e2;
+            c->E2 = ext > open ? ext : open;    if (ext > open) d |= 32;
+            open = Hleft - p.q2 - p.e2; ext = F2left - p.e2;
+            c->F2 = ext > open ? ext : open;    if (ext > open) d |= 64;
+
+            const int64_t s = (T[t] == Q[q]) ? p.a : -(int64_t)p.b;
+            const int64_t cand[5] = {Hdiag + s, c->E, c->F, c->E2, c->F2};
+            int src = 0;
+            for (int k = 1; k < 5; ++k)
+                if (cand[k] > cand[src]) src = k;      /* first of the equal ones */
+            c->H = cand[src];
+            dir[t * bw + (q - t + w)] = (uint8_t)(d | src);
+        }
+        cell_state *tmp = row_prev; row_prev = row_cur; row_cur = tmp;
+    }
+    *score_out = row_prev[end_q].H;
+
+    /* walk back from the end cell in state H */
+    enum { S_H = 0, S_E = 1, S_F = 2, S_E2 = 3, S_F2 = 4, S_DIAG = 5 };
+    orc_runs runs = {ops, 0, cap, 0, 0};
+    int64_t t = end_t, q = end_q;
+    int st = S_H;
+    while (t >= 0 && q >= 0) {
+        const uint8_t d = dir[t * bw + (q - t + w)];
+        if (st == S_H) st = (d & 7) ? (d & 7) : S_DIAG;
+        if (st == S_DIAG) {
+            orc_push(&runs, ORC_OP_M, 1); --t; --q; st = S_H;
+        } else if (st == S_E || st == S_E2) {
+            orc_push(&runs, ORC_OP_D, 1);
+            const int extended = (st == S_E) ? (d & 8) : (d & 32);
+            --t;
+            if (!extended) st = S_H;
+        } else {
+            orc_push(&runs, ORC_OP_I, 1);
+            const int extended = (st == S_F) ? (d & 16) : (d & 64);
+            --q;
+            if (!extended) st = S_H;
+        }
+    }
+    /* leading gap along the virtual row or column */
+    if (t < 0 && q >= 0) orc_push(&runs, ORC_OP_I, (uint32_t)(q + 1));
+    if (q < 0 && t >= 0) orc_push(&runs, ORC_OP_D, (uint32_t)(t + 1));
+    orc_push(&runs, 0xfu, 1);                   /* flush the last run */
+    free(dir); free(row_prev); free(row_cur);
+    if (runs.n > cap) return -1;
+    /* the runs were collected end first: reverse them */
+    const int64_t n = runs.n;
+    for (int64_t i = 0; i < n / 2; ++i) {
+        uint32_t x = ops[i]; ops[i] = ops[n - 1 - i]; ops[n - 1 - i] = x;
+    }
+    return n;
+}

@@ -5,8 +5,8 @@ benchmark's CPU-baseline leg.  The product library never loads it.
 
 Every function here marshals arguments; the arithmetic is in the C file, which
 restates the paper's recurrence (Section 2.1, Eq. 1-3, two-piece extension) and
-termination rule (Eq. 4-7).  Results are numpy structured arrays with the same
-fields as the library's result struct.
+termination rule (Eq. 4-7), and the traceback of an extension.  Results are
+numpy structured arrays with the same fields as the library's result struct.
 """
 from __future__ import annotations
 
@@ -70,6 +70,11 @@ def _load():
         lib.orc_align_batch.argtypes = [ctypes.c_void_p] * 7 + [
             ctypes.c_int64, ctypes.POINTER(_Params), ctypes.c_void_p, ctypes.c_int]
         lib.orc_result_size.restype = ctypes.c_int
+        lib.orc_traceback_pair.restype = ctypes.c_int64
+        lib.orc_traceback_pair.argtypes = [ctypes.c_void_p, ctypes.c_int32, ctypes.c_void_p,
+                                           ctypes.c_int32, ctypes.POINTER(_Params), ctypes.c_int32,
+                                           ctypes.c_int32, ctypes.c_void_p, ctypes.c_int64,
+                                           ctypes.POINTER(ctypes.c_int64)]
         assert lib.orc_result_size() == RESULT_DTYPE.itemsize
         _lib = lib
     return _lib
@@ -132,6 +137,59 @@ def align_batch(batch, idx: Optional[np.ndarray] = None, threads: Optional[int] 
     if rc != 0:
         raise RuntimeError("oracle batch failed")
     return out
+
+
+CIGAR_OPS = "MID"       # op codes 0, 1, 2 of a run (length << 4 | op)
+
+
+def end_cell(result, qlen: int):
+    """Where the traceback of an extension starts: the query end when the
+    extension reached it (reach_end), else the cell of the maximum."""
+    if result["reach_end"]:
+        return int(result["mqe_t"]), int(qlen) - 1
+    return int(result["te"]), int(result["qe"])
+
+
+def traceback_pair(target: np.ndarray, query: np.ndarray, scoring, end_t: int, end_q: int):
+    """Run-length encoded operations of the best path from the origin to
+    (end_t, end_q), and H there (0 for an empty path)."""
+    lib = _load()
+    t = np.ascontiguousarray(target, dtype=np.uint8)
+    q = np.ascontiguousarray(query, dtype=np.uint8)
+    p = _params(scoring)
+    lib.orc_normalise(ctypes.byref(p))
+    cap = len(t) + len(q) + 2
+    ops = np.zeros(cap, dtype=np.uint32)
+    score = ctypes.c_int64(0)
+    n = lib.orc_traceback_pair(t.ctypes.data if len(t) else None, len(t),
+                               q.ctypes.data if len(q) else None, len(q), ctypes.byref(p),
+                               int(end_t), int(end_q), ops.ctypes.data, cap, ctypes.byref(score))
+    if n < 0:
+        raise ValueError(f"no traceback to ({end_t}, {end_q})")
+    return ops[:n].copy(), int(score.value)
+
+
+def traceback_batch(batch, results, idx=None):
+    """CIGAR runs of every pair (or of the pairs ``idx``), from the end cells
+    the score oracle's ``results`` give.  Returns a list of uint32 arrays and
+    the H value at each end cell."""
+    idx = range(batch.n_pairs) if idx is None else idx
+    cig, scores = [], []
+    for i in idx:
+        i = int(i)
+        t = batch.t_codes[batch.t_off[i]:batch.t_off[i] + batch.t_len[i]]
+        q = batch.q_codes[batch.q_off[i]:batch.q_off[i] + batch.q_len[i]]
+        et, eq = end_cell(results[i], int(batch.q_len[i]))
+        if batch.t_len[i] <= 0 or batch.q_len[i] <= 0:
+            et = eq = -1
+        ops, sc = traceback_pair(t, q, batch.scoring, et, eq)
+        cig.append(ops)
+        scores.append(sc)
+    return cig, scores
+
+
+def cigar_string(ops) -> str:
+    return "".join(f"{int(x) >> 4}{CIGAR_OPS[int(x) & 15]}" for x in ops)
 
 
 def band_cells_full(tlen: int, qlen: int, w: int) -> int:

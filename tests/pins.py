@@ -215,3 +215,43 @@ def reference_result(T, Q, p: Dict, method: str = "brute") -> Dict:
     else:
         raise ValueError(method)
     return scan_antidiagonals(H, len(T), len(Q), p)
+
+
+def cigar_score(ops, T, Q, p: Dict, end_t: int, end_q: int) -> int:
+    """Score of an alignment given as CIGAR runs ((length << 4) | op, op
+    M=0, I=1, D=2), checked for validity along the way.
+
+    The path starts at the origin (-1,-1); it must end at (end_t, end_q),
+    visit only band cells once both indices are >= 0, and use maximal runs
+    (no two adjacent runs of one op).  Each run of I or D is one gap, scored
+    with the two-piece cost; M scores the substitution of the cell it enters.
+    Knows nothing of the E/F/E2/F2 recurrence or of the traceback rule.
+    """
+    p = normalise(p)
+    w = eff_w(p, len(T), len(Q))
+    t = q = -1
+    score = 0
+    prev = None
+    for x in ops:
+        n, op = int(x) >> 4, int(x) & 15
+        assert n >= 1 and op in (0, 1, 2), f"bad run {x:#x}"
+        assert op != prev, "adjacent runs of one op"
+        prev = op
+        if op == 0:
+            for _ in range(n):
+                t += 1
+                q += 1
+                score += p["a"] if T[t] == Q[q] else -p["b"]
+                assert abs(t - q) <= w, f"({t},{q}) outside the band"
+        else:
+            for _ in range(n):
+                if op == 1:
+                    q += 1
+                else:
+                    t += 1
+                if t >= 0 and q >= 0:
+                    assert abs(t - q) <= w, f"({t},{q}) outside the band"
+            score -= gap(p, n)
+        assert t < len(T) and q < len(Q), "path leaves the table"
+    assert (t, q) == (end_t, end_q), f"path ends at ({t},{q}), not ({end_t},{end_q})"
+    return score

@@ -127,8 +127,12 @@ def test_unmutated_oracle_passes_corpus(corpus):
 def test_mutant_is_caught(name, corpus):
     old, new = MUTANTS[name]
     src = open(SRC).read()
-    assert src.count(old) == 1, f"mutation site for {name} not found exactly once"
+    # the mistakes are planted in the score path, ahead of the traceback
+    # section (which repeats some of the boundary lines)
+    cut = src.index("Traceback of one extension")
+    head, tail = src[:cut], src[cut:]
+    assert head.count(old) == 1, f"mutation site for {name} not found exactly once"
     with tempfile.TemporaryDirectory() as d:
-        L = _compile(src.replace(old, new), d)
+        L = _compile(head.replace(old, new) + tail, d)
         caught = any(_run(L, T, Q, p) != ref for T, Q, p, ref in corpus)
     assert caught, f"planted mistake {name!r} is not caught by any pinned case"
