@@ -53,6 +53,7 @@ extern "C" {
 #define AGATHA_ECANCELED  -6   /* request cancelled by agatha_serve_stop      */
 #define AGATHA_EDEVICE    -7   /* the device reported an error status         */
 #define AGATHA_ENOTSUP    -8   /* configuration not supported                 */
+#define AGATHA_ERANGE     -9   /* caller's output buffer too small            */
 
 /* Flags for agatha_align_batch. */
 #define AGATHA_HOST_PTRS   0x00u  /* batch arrays and `out` are host memory  */
@@ -202,6 +203,60 @@ int64_t agatha_band_cells(int32_t tlen, int32_t qlen, int32_t w);
  * to these parameters (nothing to choose). */
 int agatha_tune_variants(agatha_ctx *ctx, const agatha_params *params, int32_t w_max,
                          int32_t *variants);
+
+/* ---------------------------------------------------------------------- */
+/* Traceback: the CIGAR of each extension.  The paper reports scores only;  */
+/* the traceback is the step a mapper runs next on the same banded table    */
+/* (Section 2.1, Eq. 1-3 with the two-piece gap states).                    */
+/*                                                                          */
+/* For every pair the path runs from the origin to the extension's end      */
+/* cell: (mqe_t, qlen-1) when reach_end, else (te, qe), the cell of the     */
+/* maximum; its score is mqe or max respectively.  Where several paths      */
+/* score the same, the one taken is fixed by this rule: walking back from   */
+/* the end, H(t,q) came from the first of diagonal, E, F, E2, F2 that       */
+/* equals it, and a gap state extended its predecessor's state only when    */
+/* that was strictly better than opening from the predecessor's H.  The     */
+/* virtual row/column are leading gaps (reaching (-1,q): q+1 insertions;    */
+/* (t,-1): t+1 deletions).                                                  */
+/*                                                                          */
+/* Runs are uint32 values (length << 4) | op, op AGATHA_CIGAR_M (diagonal:  */
+/* match or mismatch, one base of each), AGATHA_CIGAR_I (one query base,    */
+/* F states) or AGATHA_CIGAR_D (one target base, E states), from the start  */
+/* of the extension, adjacent runs of one op merged.                        */
+
+#define AGATHA_CIGAR_M 0u
+#define AGATHA_CIGAR_I 1u
+#define AGATHA_CIGAR_D 2u
+
+/* Align a host batch (as agatha_align_batch with AGATHA_HOST_PTRS: same
+ * results in `out`, same flags except DEVICE_PTRS/ASYNC, which give ENOTSUP)
+ * and trace every extension back.
+ *   cigar_off: host array of n_pairs + 1; pair i's runs are
+ *              cigar[cigar_off[i] .. cigar_off[i+1]).  Written on success and
+ *              on ERANGE.  A pair with an empty sequence or whose maximum is
+ *              the origin has no runs.
+ *   cigar:     host array of cigar_cap runs.  The runs of pair i number at
+ *              most t_len[i] + q_len[i]; on ERANGE (cigar_off[n] > cap)
+ *              nothing is written to it.
+ * Device memory: besides the score path's buffers, a direction table of one
+ * byte per band slot and anti-diagonal up to each end cell (32*C bytes per
+ * anti-diagonal, C the int32 kernel's slots per lane for the batch's widest
+ * band: 4, 8, 16, 24 or 32).  Pairs run in waves whose tables fit in the
+ * context's budget (else in the device's free memory less min(1/16 of it,
+ * 4 GiB)); the context keeps the largest table made until agatha_destroy.
+ * Errors: EINVAL (bad batch or parameters), ENOTSUP (a band wider than 1023
+ * cells, or device pointers), ENOMEM (one pair's table does not fit), ERANGE,
+ * ECUDA. */
+int agatha_align_cigar(agatha_ctx *ctx, const agatha_batch *batch,
+                       const agatha_params *params, agatha_result *out,
+                       int64_t *cigar_off, uint32_t *cigar, int64_t cigar_cap,
+                       uint32_t flags, void *stream);
+
+/* Duration in milliseconds of the traceback kernels (all waves, between CUDA
+ * events on the call's stream) of the last agatha_align_cigar call on ctx;
+ * agatha_last_kernel_ms gives its score kernels.  ENOTSUP without
+ * AGATHA_CFG_TIMING, EAGAIN before the first traceback. */
+int agatha_last_traceback_ms(agatha_ctx *ctx, float *ms);
 
 /* ---------------------------------------------------------------------- */
 /* Serving: continuous batching of alignment requests on one device.       */

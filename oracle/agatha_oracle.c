@@ -312,14 +312,19 @@ int64_t orc_traceback_pair(const uint8_t *T, int32_t tlen, const uint8_t *Q, int
     cell_state *row_prev = (cell_state *)malloc(sizeof(cell_state) * (size_t)nq);
     cell_state *row_cur = (cell_state *)malloc(sizeof(cell_state) * (size_t)nq);
     if (!dir || !row_prev || !row_cur) { free(dir); free(row_prev); free(row_cur); return -1; }
+    const cell_state outside = {ORC_MINUS_INF, ORC_MINUS_INF, ORC_MINUS_INF, ORC_MINUS_INF, ORC_MINUS_INF};
+    for (int64_t q = 0; q < nq; ++q) row_prev[q] = row_cur[q] = outside;
 
     for (int64_t t = 0; t < nt; ++t) {
-        for (int64_t q = 0; q < nq; ++q) {
+        /* row t's band cells are q in [lo, hi].  Entries of the row arrays
+           outside the previous row's band hold minus infinity: index hi of
+           row_prev was never written (earlier bands end further left) and
+           index lo-1 of row_cur, left over from row t-2, is reset here. */
+        const int64_t lo = t - w > 0 ? t - w : 0;
+        const int64_t hi = t + w < nq - 1 ? t + w : nq - 1;
+        if (lo > 0) row_cur[lo - 1] = outside;
+        for (int64_t q = lo; q <= hi; ++q) {
             cell_state *c = &row_cur[q];
-            if (!in_band(t, q, tlen, qlen, w)) {
-                c->H = c->E = c->F = c->E2 = c->F2 = ORC_MINUS_INF;
-                continue;
-            }
             /* predecessors, with the virtual row/column of Section 2.1's
                extension boundary and minus infinity outside the band */
             int64_t Hdiag;

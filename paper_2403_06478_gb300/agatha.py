@@ -27,6 +27,7 @@ AGATHA_EAGAIN = -5
 AGATHA_ECANCELED = -6
 AGATHA_EDEVICE = -7
 AGATHA_ENOTSUP = -8
+AGATHA_ERANGE = -9
 
 AGATHA_HOST_PTRS = 0x00
 AGATHA_DEVICE_PTRS = 0x01
@@ -41,6 +42,12 @@ AGATHA_NO_TUNE = 0x100
 
 AGATHA_CFG_TIMING = 0x1
 AGATHA_CFG_AUTOTUNE = 0x2
+
+# CIGAR run op codes ((length << 4) | op)
+AGATHA_CIGAR_M = 0
+AGATHA_CIGAR_I = 1
+AGATHA_CIGAR_D = 2
+CIGAR_OPS = "MID"
 
 # kernel variants the autotuner chooses between, per length class
 VARIANT_NAMES = ("int16x2", "int16x2-highreg", "int32")
@@ -128,6 +135,11 @@ _SIGS = {
     "agatha_version": (ctypes.c_int32, []),
     "agatha_tune_variants": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(agatha_params),
                                             ctypes.c_int32, ctypes.POINTER(ctypes.c_int32)]),
+    "agatha_align_cigar": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(agatha_batch),
+                                          ctypes.POINTER(agatha_params), ctypes.c_void_p,
+                                          ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64,
+                                          ctypes.c_uint32, ctypes.c_void_p]),
+    "agatha_last_traceback_ms": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_float)]),
 }
 
 
@@ -299,6 +311,32 @@ class Context:
         _check(rc, self._ptr, "agatha_align_batch")
         return out
 
+    def align_cigar(self, pb: PackedBatch, scoring, flags: int = 0, stream: int = 0,
+                    cigar_cap: Optional[int] = None):
+        """agatha_align_cigar with host arrays.  Returns (results, cigar_off,
+        cigar): pair i's runs are cigar[cigar_off[i]:cigar_off[i + 1]].  The
+        default capacity (t_len + q_len summed) always suffices."""
+        n = pb.n_pairs
+        out = np.zeros(n, dtype=RESULT_DTYPE)
+        off = np.zeros(n + 1, dtype=np.int64)
+        if cigar_cap is None:
+            cigar_cap = int(np.asarray(pb.t_len, np.int64).sum() + np.asarray(pb.q_len, np.int64).sum())
+        cigar = np.empty(max(int(cigar_cap), 1), dtype=np.uint32)
+        b = _host_batch(pb)
+        p = make_params(scoring)
+        rc = lib().agatha_align_cigar(self._ptr, ctypes.byref(b), ctypes.byref(p),
+                                      out.ctypes.data if n else None, off.ctypes.data,
+                                      cigar.ctypes.data, ctypes.c_int64(int(cigar_cap)),
+                                      ctypes.c_uint32(flags), ctypes.c_void_p(stream) if stream else None)
+        _check(rc, self._ptr, "agatha_align_cigar")
+        return out, off, cigar[: int(off[-1])]
+
+    def last_traceback_ms(self) -> float:
+        ms = ctypes.c_float()
+        _check(lib().agatha_last_traceback_ms(self._ptr, ctypes.byref(ms)), self._ptr,
+               "agatha_last_traceback_ms")
+        return float(ms.value)
+
     def align_device(self, q_packed, t_packed, q_off, t_off, q_len, t_len, out, scoring,
                      flags: int = 0, stream: int = 0) -> None:
         """agatha_align_batch on device tensors (torch CUDA tensors or raw pointers).
@@ -425,3 +463,8 @@ def results_equal(a: np.ndarray, b: np.ndarray, fields: Sequence[str] = RESULT_F
     for f in fields:
         bad |= a[f] != b[f]
     return np.flatnonzero(bad)
+
+
+def cigar_string(runs) -> str:
+    """SAM-style text of CIGAR runs ((length << 4) | op)."""
+    return "".join(f"{int(x) >> 4}{CIGAR_OPS[int(x) & 15]}" for x in runs)

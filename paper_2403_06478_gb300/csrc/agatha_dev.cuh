@@ -204,6 +204,13 @@ __device__ __forceinline__ WorkList work_list(const DevBatch &B, int32_t list) {
     return L;
 }
 
+// One pair of a traceback launch: its end cell (from the score path) and
+// where its direction table (bytes) and run scratch (uint32) start.
+struct TbItem {
+    int32_t pair, end_t, end_q, pad;
+    int64_t dir_off, ops_off;
+};
+
 // Launchers (defined in the .cu files).
 cudaError_t launch_prep(const DevBatch *d_batch, int64_t n_pairs, int32_t sort, cudaStream_t s,
                         int n_sm);
@@ -218,6 +225,15 @@ cudaError_t launch_warp16_c(const DevBatch *d_batch, int n_blocks, cudaStream_t 
                             int list = WARP_LIST_MAIN);
 template <int C, int MINB>
 int occupancy_warp16_c();
+template <int C>
+cudaError_t launch_tb_c(const DevBatch *d_batch, const TbItem *items, int32_t n_items, int32_t *head,
+                        uint8_t *dir, uint32_t *ops, int32_t *n_cigar, int n_blocks, cudaStream_t s);
+template <int C>
+int occupancy_tb_c();
+// Copy each pair's runs (written end first) to dense[dst_off[pair]..] in order.
+cudaError_t launch_cigar_gather(const TbItem *items, int32_t n_items, const int32_t *n_cigar,
+                                const int64_t *dst_off, const uint32_t *ops, uint32_t *dense,
+                                int n_blocks, cudaStream_t s);
 cudaError_t launch_plain_kernel(const DevBatch *d_batch, int64_t n_blocks, int32_t w_max,
                                 int use_wide_list, cudaStream_t s);
 int plain_kernel_max_w();

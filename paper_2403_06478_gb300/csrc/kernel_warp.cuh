@@ -18,6 +18,14 @@
 // Steps near the table's edges (the first w+4 anti-diagonals, where virtual
 // row/column cells enter, and the ones that touch t = tlen-1 or q = qlen-1)
 // run a masked variant; the bulk in between runs unmasked.
+//
+// With DIR the same steps also record, per band slot and anti-diagonal, one
+// direction byte for the traceback (kernel_tb.cuh) and run to a given end
+// anti-diagonal instead of testing termination:
+//   bits 0-2  which input H took: 0 diagonal, 1 E, 2 F, 3 E2, 4 F2 (the first
+//             of these that equals H)
+//   bits 3-6  whether Eo, Fo, E2o, F2o leaving this cell extend the cell's
+//             own E, F, E2, F2 (strictly better than opening from H)
 #pragma once
 
 #include <climits>
@@ -37,9 +45,10 @@ struct WarpWin {
     static constexpr T LOW = (sizeof(T) == 4) ? T(0x55555555u) : T(0x5555555555555555ull);
 };
 
-template <int C>
+template <int C, bool DIR = false>
 struct WarpPair {
     using W = typename WarpWin<C>::T;
+    static constexpr int32_t DIR_ROW = 32 * C;   // direction bytes per anti-diagonal
     // static pair data
     const uint32_t *tp, *qp;
     int64_t tw, qw, toff, qoff;
@@ -57,6 +66,35 @@ struct WarpPair {
     int32_t gmax, gt, gq, mqe, mqe_t, mte, mte_q, gscore;
     int64_t cells;
     int32_t zdropped;
+    uint8_t *dtab;           // DIR: this lane's bytes of anti-diagonal 0
+
+    // DIR: the direction byte of one cell (see the top of this file)
+    __device__ __forceinline__ uint32_t dir_bits(int32_t hd, int32_t Ein, int32_t Fin, int32_t E2in,
+                                                 int32_t F2in, int32_t H, int32_t hoe,
+                                                 int32_t hoe2) const {
+        uint32_t b = H == hd ? 0u : (H == Ein ? 1u : (H == Fin ? 2u : (H == E2in ? 3u : 4u)));
+        b |= (Ein - P.e > hoe) ? 8u : 0u;
+        b |= (Fin - P.e > hoe) ? 16u : 0u;
+        b |= (E2in - P.e2 > hoe2) ? 32u : 0u;
+        b |= (F2in - P.e2 > hoe2) ? 64u : 0u;
+        return b;
+    }
+
+    // DIR: this lane's C bytes of anti-diagonal r, one aligned vector store
+    __device__ __forceinline__ void store_dir(int32_t r, const uint32_t (&wd)[C / 4]) const {
+        uint8_t *p = dtab + (int64_t)r * DIR_ROW;
+        if constexpr (C % 16 == 0) {
+#pragma unroll
+            for (int k = 0; k < C / 16; ++k)
+                reinterpret_cast<uint4 *>(p)[k] = make_uint4(wd[4 * k], wd[4 * k + 1], wd[4 * k + 2], wd[4 * k + 3]);
+        } else if constexpr (C % 8 == 0) {
+#pragma unroll
+            for (int k = 0; k < C / 8; ++k)
+                reinterpret_cast<uint2 *>(p)[k] = make_uint2(wd[2 * k], wd[2 * k + 1]);
+        } else {
+            *reinterpret_cast<uint32_t *>(p) = wd[0];
+        }
+    }
 
     __device__ __forceinline__ void init_windows(int32_t r) {
         const int32_t B = ceil_div2(r - w);
@@ -132,7 +170,7 @@ struct WarpPair {
     __device__ __forceinline__ bool masked_step(int32_t r) {
         const int32_t B = ceil_div2(r - w);
         const int32_t d = (r - w) & 1;
-        if (r >= 0) {
+        if (!DIR && r >= 0) {
             const int32_t st = max(max(0, r - qlen + 1), B);
             const int32_t en = min(min(tlen - 1, r), floor_div2(r + w));
             if (st > en) { zdropped = 1; return true; }    // the band left the table
@@ -157,6 +195,9 @@ struct WarpPair {
         const W x = Tw ^ Qw;
         const W nm = (x | (x >> 1)) & WarpWin<C>::LOW;     // bit 2*jl: mismatch
         int32_t nH[C], nE[C], nE2[C], nF[C], nF2[C];
+        uint32_t wd[C / 4];
+#pragma unroll
+        for (int k = 0; k < C / 4; ++k) wd[k] = 0;
         int32_t lm = INT_MIN, li = -1, te_c = INT_MIN, qe_c = INT_MIN;
 #pragma unroll
         for (int jl = 0; jl < C; ++jl) {
@@ -171,6 +212,8 @@ struct WarpPair {
             int32_t hoe = H - oe, hoe2 = H - oe2;
             int32_t ne = max(hoe, Ein - P.e), nf = max(hoe, Fin - P.e);
             int32_t ne2 = max(hoe2, E2in - P.e2), nf2 = max(hoe2, F2in - P.e2);
+            if constexpr (DIR)
+                wd[jl >> 2] |= dir_bits(H2[jl] + s, Ein, Fin, E2in, F2in, H, hoe, hoe2) << (8 * (jl & 3));
             const int32_t k = t - q;
             const bool real = t >= 0 && q >= 0 && t < tlen && q < qlen && k <= w && -k <= w;
             if (real) {
@@ -194,6 +237,10 @@ struct WarpPair {
             Eo[jl] = nE[jl]; E2o[jl] = nE2[jl]; Fo[jl] = nF[jl]; F2o[jl] = nF2[jl];
         }
         if (r < 0) return false;
+        if constexpr (DIR) {
+            store_dir(r, wd);
+            return false;
+        }
         // last target row / last query column
         const int32_t te_v = __reduce_max_sync(FULL, te_c);
         if (te_v != INT_MIN && te_v > mte) { mte = te_v; mte_q = r - (tlen - 1); }
@@ -224,6 +271,9 @@ struct WarpPair {
         const W x = Tw ^ Qw;
         const W nm = (x | (x >> 1)) & WarpWin<C>::LOW;
         int32_t nH[C], nE[C], nE2[C], nF[C], nF2[C];
+        uint32_t wd[C / 4];
+#pragma unroll
+        for (int k = 0; k < C / 4; ++k) wd[k] = 0;
         int32_t lm = INT_MIN, li = -1;
 #pragma unroll
         for (int jl = 0; jl < C; ++jl) {
@@ -238,6 +288,8 @@ struct WarpPair {
             // flows back into the band; their E states only flow further out
             const int32_t hoe = valid ? H - oe : K_NEG;
             const int32_t hoe2 = valid ? H - oe2 : K_NEG;
+            if constexpr (DIR)
+                wd[jl >> 2] |= dir_bits(H2[jl] + s, Ein, Fin, E2in, F2in, H, hoe, hoe2) << (8 * (jl & 3));
             nE[jl] = max(hoe, Ein - P.e);
             nF[jl] = max(hoe, Fin - P.e);
             nE2[jl] = max(hoe2, E2in - P.e2);
@@ -249,6 +301,10 @@ struct WarpPair {
         for (int jl = 0; jl < C; ++jl) {
             H2[jl] = H1[jl]; H1[jl] = nH[jl];
             Eo[jl] = nE[jl]; E2o[jl] = nE2[jl]; Fo[jl] = nF[jl]; F2o[jl] = nF2[jl];
+        }
+        if constexpr (DIR) {
+            store_dir(r, wd);
+            return false;
         }
         cells += w + 1 - D;
         int32_t m, tstar;
@@ -315,6 +371,52 @@ struct WarpPair {
             o.lane16 = 0;
             for (int i = 0; i < 5; ++i) o.pad[i] = 0;
             *out = o;
+        }
+    }
+
+    // DIR: anti-diagonals 0..r_end of a pair with its direction bytes in
+    // dt[r * DIR_ROW + slot] (no termination test: r_end is known).
+    __device__ __forceinline__ void run_dir(const DevBatch &Bt, int32_t pair, int32_t lane_,
+                                            int32_t r_end, uint8_t *dt) {
+        static_assert(DIR, "run_dir needs the direction variant");
+        P = Bt.params;
+        lane = lane_;
+        tp = Bt.t_packed; qp = Bt.q_packed; tw = Bt.t_words; qw = Bt.q_words;
+        tlen = Bt.t_len[pair]; qlen = Bt.q_len[pair];
+        toff = Bt.t_off[pair]; qoff = Bt.q_off[pair];
+        w = effective_w(P.w, tlen, qlen);
+        oe = P.q + P.e; oe2 = P.q2 + P.e2;
+        j0 = lane * C;
+        last_r = r_end;
+        dtab = dt + j0;
+#pragma unroll
+        for (int i = 0; i < C; ++i) { H1[i] = H2[i] = Eo[i] = E2o[i] = Fo[i] = F2o[i] = K_NEG; }
+        cells = 0; zdropped = 0;
+        int32_t r = -2;
+        init_windows(r);
+        masked_step(r);
+        const int32_t head_end = min(last_r, w + 1);
+        while (r < head_end) {
+            ++r;
+            if ((r - w) & 1) shift_t(); else shift_q();
+            masked_step(r);
+        }
+        const int32_t L = min(tlen, qlen);
+        const int32_t bulk_last = min(2 * L - 3 - w, last_r);
+        if (r == w + 1) {
+            const int32_t vcnt0 = max(0, min(C, w + 1 - j0));
+            const int32_t vcnt1 = max(0, min(C, w - j0));
+            while (r + 2 <= bulk_last) {
+                ++r; shift_q();
+                fast_step<0>(r, vcnt0);
+                ++r; shift_t();
+                fast_step<1>(r, vcnt1);
+            }
+        }
+        while (r < last_r) {
+            ++r;
+            if ((r - w) & 1) shift_t(); else shift_q();
+            masked_step(r);
         }
     }
 };

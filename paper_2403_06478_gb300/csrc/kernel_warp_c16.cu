@@ -1,7 +1,10 @@
-// Instantiation of the warp kernel for 16 band slots per lane (w <= 511).
-#include "kernel_warp.cuh"
+// Instantiation of the warp kernel and its traceback variant for 16 band slots per lane (w <= 511).
+#include "kernel_tb.cuh"
 
 namespace agatha {
 template cudaError_t launch_warp_c<16>(const DevBatch *, int, cudaStream_t, int, int);
 template int occupancy_warp_c<16>();
+template cudaError_t launch_tb_c<16>(const DevBatch *, const TbItem *, int32_t, int32_t *, uint8_t *,
+                                    uint32_t *, int32_t *, int, cudaStream_t);
+template int occupancy_tb_c<16>();
 }  // namespace agatha

@@ -30,6 +30,7 @@ const char *agatha_strerror(int code) {
         case AGATHA_ECANCELED: return "cancelled";
         case AGATHA_EDEVICE: return "device reported an error";
         case AGATHA_ENOTSUP: return "not supported";
+        case AGATHA_ERANGE: return "output buffer too small";
         default: return "unknown error";
     }
 }
@@ -503,6 +504,9 @@ extern "C" void agatha_destroy(agatha_ctx *ctx) {
     cudaSetDevice(ctx->device);
     if (ctx->stream) cudaStreamSynchronize(ctx->stream);
     slot_release(ctx->ledger, &ctx->main);
+    ctx->tb.release(ctx->ledger);
+    if (ctx->ev_tb0) cudaEventDestroy(ctx->ev_tb0);
+    if (ctx->ev_tb1) cudaEventDestroy(ctx->ev_tb1);
     if (ctx->tune_ev0) cudaEventDestroy(ctx->tune_ev0);
     if (ctx->tune_ev1) cudaEventDestroy(ctx->tune_ev1);
     if (ctx->ev_k0) cudaEventDestroy(ctx->ev_k0);

@@ -90,6 +90,15 @@ struct Slot {
     std::map<std::tuple<int, PlanKey>, cudaGraphExec_t> graphs;
 };
 
+// Device buffers of the traceback path (tb.cu), kept for later calls.
+struct TbBufs {
+    DevBuf dir, ops, items, n_cigar, heads, dst_off, dense;
+    void release(Ledger &ledger) {
+        DevBuf *b[] = {&dir, &ops, &items, &n_cigar, &heads, &dst_off, &dense};
+        for (DevBuf *x : b) x->release(ledger);
+    }
+};
+
 int set_error(agatha_ctx *ctx, int code, const char *fmt, ...);
 int cuda_fail(agatha_ctx *ctx, cudaError_t e, const char *what);
 int normalise_params(const agatha_params *in, DevParams *out);
@@ -149,4 +158,7 @@ struct agatha_ctx {
     std::mutex tune_mu;                // guards tune_table (align_batch and the server read it)
     std::map<std::string, agatha::TuneChoice> tune_table;
     cudaEvent_t tune_ev0 = nullptr, tune_ev1 = nullptr;
+    agatha::TbBufs tb;                 // traceback buffers (agatha_align_cigar)
+    cudaEvent_t ev_tb0 = nullptr, ev_tb1 = nullptr;
+    bool tb_timed = false;
 };
