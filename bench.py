@@ -16,6 +16,8 @@ w=500, zdrop=400).  Printed as one JSON line:
 
 ``--workload hifi|skewed|small`` measures another configuration with the same
 metric (the ONT-like batch is the default and the headline).
+``--traceback`` measures the path with its CIGARs (agatha_align_cigar): the
+score kernels plus the direction-recording traceback kernel.
 ``--impl reference`` times the CPU oracle as the reference arm instead.
 Multi-GPU (torchrun): every rank aligns its own batch (weak scaling, no
 collective on the data path); rank 0 prints the aggregate.
@@ -56,6 +58,9 @@ L2_FLUSH_BYTES = 512 << 20          # > 129 MB of L2
 # 16x2 lane op serves two cells
 OPS_PER_CELL_I32 = 13.0
 OPS_PER_CELL_I16X2 = 6.5
+# traceback kernel: the int32 cell ops plus the direction byte (H source:
+# four compare-selects; four gap-continuation compares; one byte insert)
+OPS_PER_CELL_TB = OPS_PER_CELL_I32 + 9.0
 CPU_SAMPLE_PAIRS = 6000
 CPU_SAMPLE_CELLS = 4e10             # about 12 s of the oracle on 16 cores
 REF_STEP_PAIRS = 300
@@ -216,6 +221,118 @@ def run_reference(args):
     return 0
 
 
+def traceback_cells(res, batch):
+    """Band cells on anti-diagonals 0..r_end of every pair's traceback (the
+    cells the traceback kernel computes), r_end the end cell's anti-diagonal."""
+    w_all = batch.scoring.w
+    total = 0
+    for i in range(batch.n_pairs):
+        tl, ql = int(batch.t_len[i]), int(batch.q_len[i])
+        r = res[i]
+        et, eq = (int(r["mqe_t"]), ql - 1) if r["reach_end"] else (int(r["te"]), int(r["qe"]))
+        if tl <= 0 or ql <= 0 or et < 0 or eq < 0:
+            continue
+        w = w_all if 0 <= w_all <= max(tl, ql) else max(tl, ql)
+        rr = np.arange(et + eq + 1, dtype=np.int64)
+        st = np.maximum(np.maximum(0, rr - ql + 1), -((w - rr) // 2))
+        en = np.minimum(np.minimum(tl - 1, rr), (rr + w) // 2)
+        total += int(np.maximum(0, en - st + 1).sum())
+    return total
+
+
+def run_traceback(args):
+    """The path with CIGARs through agatha_align_cigar (host buffers only).
+
+    value = score cells / (score kernels + traceback kernels), CUDA events on
+    the call's stream; e2e = the same cells / the whole call (copies both
+    ways, host planning between the passes), both from pinned host buffers."""
+    import torch
+    from paper_2403_06478_gb300 import agatha as A
+    from paper_2403_06478_gb300 import build as B
+    from paper_2403_06478_gb300 import workload as W
+    rank, world, local = _env_int("RANK", 0), _env_int("WORLD_SIZE", 1), _env_int("LOCAL_RANK", 0)
+    torch.cuda.set_device(local)
+    B.build()
+    batch = W.make_config(args.workload, seed=None if rank == 0 else W.SEED_BASE + 2 + 1000 * rank)
+    pb = A.pack_batch(batch)
+    pin = {k: torch.from_numpy(getattr(pb, k)).pin_memory() for k in
+           ("q_packed", "t_packed", "q_off", "t_off", "q_len", "t_len")}
+    pin_pb = A.PackedBatch(*[pin[k].numpy() for k in
+                             ("q_packed", "t_packed", "q_off", "t_off", "q_len", "t_len")])
+    stream = torch.cuda.Stream()
+    torch.cuda.set_stream(stream)
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device="cuda")
+    free0, total0 = torch.cuda.mem_get_info(local)
+    ctx = A.Context(local, timing=True, autotune=True, tune_cache_path=args.tune_cache)
+    ctx.align_host(pb, batch.scoring)                     # autotune the score path
+    for _ in range(args.warmup):
+        res, off, cig = ctx.align_cigar(pin_pb, batch.scoring, stream=stream.cuda_stream)
+    sampler = ClockSampler(local)
+    sampler.start()
+    wall_ms, score_ms, tb_ms = [], [], []
+    for k in range(args.steps):
+        flush.fill_(k & 0xff)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        res, off, cig = ctx.align_cigar(pin_pb, batch.scoring, stream=stream.cuda_stream)
+        wall_ms.append((time.perf_counter() - t0) * 1e3)
+        score_ms.append(ctx.last_kernel_ms())
+        tb_ms.append(ctx.last_traceback_ms())
+    clocks = sampler.stop()
+    alone = A.agatha_align_batch(ctx, batch)
+    exact = bool(A.results_equal(res, alone).size == 0)
+    cells = int(res["cells"].sum())
+    tcells = traceback_cells(res, batch)
+    n = pb.n_pairs
+    k_ms = statistics.mean(score_ms) + statistics.mean(tb_ms)
+    peaks, peak_kind = measured_peaks()
+    n_sm = torch.cuda.get_device_properties(local).multi_processor_count
+    sm_max_mhz = float(peaks.get("sm_max_mhz", 2070.0))
+    int_peak = n_sm * 128 * sm_max_mhz * 1e6 / 1e12
+    t_ms = statistics.mean(tb_ms)
+    achieved = tcells * OPS_PER_CELL_TB / (t_ms / 1e3) / 1e12
+    w = batch.scoring.w
+    C = next(c for c in (4, 8, 16, 24, 32) if 32 * c - 1 >= w)
+    table_bytes = sum(((int(r["mqe_t"]) + int(batch.q_len[i]) - 1) if r["reach_end"] else
+                       (int(r["te"]) + int(r["qe"]))) + 1 for i, r in enumerate(res)
+                      if batch.t_len[i] > 0 and batch.q_len[i] > 0 and
+                      (r["reach_end"] or r["te"] >= 0)) * 32 * C
+    line = {
+        "metric": "GCUPS with traceback (score path + CIGAR of every extension), bit-exact",
+        "value": round(cells / (k_ms / 1e3) / 1e9, 3), "unit": "GCUPS", "n_gpus": 1,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(k_ms, 3),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int32",
+        "data": "synthetic",
+        "config": {"workload": WORKLOADS[args.workload], "pairs_per_gpu": n, "cells_per_step": cells,
+                   "traceback_cells_per_step": tcells, "cigar_runs_per_step": int(off[-1]),
+                   "direction_table_bytes": int(table_bytes),
+                   "l2": "flushed between steps (512 MB write)",
+                   "value_basis": "score kernels + traceback kernels, CUDA events"},
+        "pairs_per_s": round(n / (k_ms / 1e3), 1),
+        "score_kernel_ms": round(statistics.mean(score_ms), 3),
+        "traceback_kernel_ms": round(t_ms, 3),
+        "results_equal_score_path": exact,
+        "e2e": {"value": round(cells / (statistics.mean(wall_ms) / 1e3) / 1e9, 3), "unit": "GCUPS",
+                "h2d_bytes_per_step": int(pin_pb.nbytes()),
+                "d2h_bytes_per_step": int(n * 48 + 4 * n + 4 * int(off[-1])),
+                "ms_per_step": round(statistics.mean(wall_ms), 3)},
+        # score path (prep 3, 16-bit kernel, overflow kernel), one traceback
+        # launch per wave (tables up to the free memory less min(1/16, 4 GiB)),
+        # the CIGAR gather
+        "gpu_launches": args.steps * (5 + -(-table_bytes // max(1, free0 - min(total0 // 16, 4 << 30)
+                                                             - (1 << 30))) + 1),
+        "roofline": {"bound": "alu", "achieved": round(achieved, 3), "peak": round(int_peak, 3),
+                     "unit": "Tops/s", "frac": round(achieved / int_peak, 4), "traffic": None,
+                     "kernel": f"tb_kernel<{C}>", "kernel_ms": round(t_ms, 3),
+                     "ops_per_cell": OPS_PER_CELL_TB,
+                     "peak_basis": f"{n_sm} SMs x 128 int32 lanes x {sm_max_mhz:.0f} MHz ({peak_kind})"},
+        "clocks": clocks,
+    }
+    print(json.dumps(line), flush=True)
+    ctx.close()
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -229,10 +346,14 @@ def main():
                     help="autotuner cache file: read if present, written after tuning")
     ap.add_argument("--workload", default="ont", choices=sorted(WORKLOADS),
                     help="ont (the headline), or another configuration of the same metric")
+    ap.add_argument("--traceback", action="store_true",
+                    help="the path with CIGARs: score kernels + traceback kernel")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     if args.impl == "reference":
         return run_reference(args)
+    if args.traceback:
+        return run_traceback(args)
 
     import torch
     from paper_2403_06478_gb300 import agatha as A

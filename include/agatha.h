@@ -238,12 +238,18 @@ int agatha_tune_variants(agatha_ctx *ctx, const agatha_params *params, int32_t w
  *   cigar:     host array of cigar_cap runs.  The runs of pair i number at
  *              most t_len[i] + q_len[i]; on ERANGE (cigar_off[n] > cap)
  *              nothing is written to it.
+ * Kernels: the traceback recomputes each band up to its end cell and
+ * records one direction byte per slot, on 16-bit packed lanes when the
+ * scoring allows them (as for the score path; AGATHA_FORCE32 turns them off)
+ * and on int32 lanes otherwise or for a pair whose scores leave the 16-bit
+ * range; both give the same CIGARs.
  * Device memory: besides the score path's buffers, a direction table of one
  * byte per band slot and anti-diagonal up to each end cell (32*C bytes per
- * anti-diagonal, C the int32 kernel's slots per lane for the batch's widest
- * band: 4, 8, 16, 24 or 32).  Pairs run in waves whose tables fit in the
- * context's budget (else in the device's free memory less min(1/16 of it,
- * 4 GiB)); the context keeps the largest table made until agatha_destroy.
+ * anti-diagonal, C the kernel's slots per lane for the batch's widest band:
+ * 4, 8, 16 or 24 on 16-bit lanes, up to 32 on int32 lanes).  Pairs run in
+ * waves whose tables fit in the context's budget (else in the device's free
+ * memory less min(1/16 of it, 4 GiB)); the context keeps the largest table
+ * made until agatha_destroy.
  * Errors: EINVAL (bad batch or parameters), ENOTSUP (a band wider than 1023
  * cells, or device pointers), ENOMEM (one pair's table does not fit), ERANGE,
  * ECUDA. */
@@ -257,6 +263,14 @@ int agatha_align_cigar(agatha_ctx *ctx, const agatha_batch *batch,
  * agatha_last_kernel_ms gives its score kernels.  ENOTSUP without
  * AGATHA_CFG_TIMING, EAGAIN before the first traceback. */
 int agatha_last_traceback_ms(agatha_ctx *ctx, float *ms);
+
+/* What the last agatha_align_cigar call on ctx ran: pairs given to the
+ * 16-bit traceback kernel, pairs the int32 kernel traced (including those
+ * the 16-bit kernel handed back), and kernel launches (waves). */
+typedef struct {
+    int64_t pairs16, pairs32, waves, pad;
+} agatha_tb_info;
+int agatha_last_traceback_info(agatha_ctx *ctx, agatha_tb_info *info);
 
 /* ---------------------------------------------------------------------- */
 /* Serving: continuous batching of alignment requests on one device.       */

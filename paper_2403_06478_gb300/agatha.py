@@ -105,6 +105,11 @@ class agatha_serve_stats(ctypes.Structure):
                 ("p99_latency_ms", ctypes.c_double)]
 
 
+class agatha_tb_info(ctypes.Structure):
+    _fields_ = [("pairs16", ctypes.c_int64), ("pairs32", ctypes.c_int64), ("waves", ctypes.c_int64),
+                ("pad", ctypes.c_int64)]
+
+
 _lib = None
 
 # every function the header declares, with its ctypes signature
@@ -140,6 +145,7 @@ _SIGS = {
                                           ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64,
                                           ctypes.c_uint32, ctypes.c_void_p]),
     "agatha_last_traceback_ms": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_float)]),
+    "agatha_last_traceback_info": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(agatha_tb_info)]),
 }
 
 
@@ -330,6 +336,12 @@ class Context:
                                       ctypes.c_uint32(flags), ctypes.c_void_p(stream) if stream else None)
         _check(rc, self._ptr, "agatha_align_cigar")
         return out, off, cigar[: int(off[-1])]
+
+    def last_traceback_info(self) -> dict:
+        info = agatha_tb_info()
+        _check(lib().agatha_last_traceback_info(self._ptr, ctypes.byref(info)), self._ptr,
+               "agatha_last_traceback_info")
+        return {"pairs16": int(info.pairs16), "pairs32": int(info.pairs32), "waves": int(info.waves)}
 
     def last_traceback_ms(self) -> float:
         ms = ctypes.c_float()

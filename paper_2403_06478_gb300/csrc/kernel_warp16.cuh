@@ -94,7 +94,16 @@ struct Cold16 {
 // next Z-drop test and when the bulk loop ends; until then the H values of its
 // anti-diagonal are kept, so a run of growing maxima costs one copy each
 // instead of one search each.
-template <int C, bool DMREG, bool DEFER = false>
+// DIR: the traceback variant (kernel_tb.cuh).  The same steps, run to a given
+// end anti-diagonal without the termination test, also write one direction
+// byte per slot: register p's low and high halves give bytes 2p and 2p+1 of
+// the lane's C bytes of the anti-diagonal's row (slots j0+p and j0+p+P).
+//   bits 0-3  H differs from the diagonal input H(r-2)+s, from E, F, E2
+//             (H took the first input it equals; F2 if it differs from all four)
+//   bits 4-7  Eo, Fo, E2o, F2o leaving the cell extend the cell's own gap
+//             state (strictly better than opening from H)
+// Each bit is one 16x2 minimum of an exclusive or (0 or 1 per half).
+template <int C, bool DMREG, bool DEFER = false, bool DIR = false>
 struct WarpPair16 {
     static_assert(C == 4 || C == 8 || C == 16 || C == 24, "16-bit lanes use 4, 8, 16 or 24 slots per lane");
     static constexpr int P = C / 2;
@@ -123,6 +132,7 @@ struct WarpPair16 {
     uint32_t DF2;
     uint32_t DMR[DMREG ? P : 1];   // DMREG: dead_mask(p), computed once per pair
     uint32_t Hsave[DEFER ? P : 1]; // DEFER: H of the pending maximum's anti-diagonal
+    uint8_t *dtab;                 // DIR: this lane's bytes of anti-diagonal 0
     int32_t pend_r, pend_m, pend_lm;   // its anti-diagonal (-3: none), maximum, lane maximum
     // base windows (2 bits per slot): Tw field jl = T[B + j0 + jl],
     // Qw field jl = Q[r - B - j0 - jl]
@@ -413,6 +423,7 @@ struct WarpPair16 {
         }
         const Comb comb = packed_mismatch();
         uint32_t lmax = 0, pend = 0;
+        uint32_t dbits[DIR ? P : 1];
 #pragma unroll
         for (int i = 0; i < P; ++i) {
             const int p = ODD ? P - 1 - i : i;
@@ -434,6 +445,14 @@ struct WarpPair16 {
             // H = max(H(r-2) + s, E, F, E2, F2): add-max, 3-input max, max
             const uint32_t H = __vmaxu2(__vimax3_u16x2(__viaddmax_u16x2(Hd[p], s2, Ein), Fin, E2in),
                                         F2in);
+            if constexpr (DIR) {
+                // 1 per half where H differs from the input (scores sit far
+                // above 0, so the per-half add of s needs no further clamp)
+                const uint32_t one = 0x10001u;
+                const uint32_t hd = __viaddmax_u16x2(Hd[p], s2, 0u);
+                dbits[p] = __vminu2(H ^ hd, one) + (__vminu2(H ^ Ein, one) << 1) +
+                           (__vminu2(H ^ Fin, one) << 2) + (__vminu2(H ^ E2in, one) << 3);
+            }
             uint32_t mx;                          // this register's share of the maximum
             if constexpr (MODE != HEAD) {
                 const uint32_t dead = dead_mask_r<ODD>(p);
@@ -446,6 +465,7 @@ struct WarpPair16 {
                 F2o[p] = __viaddmax_u16x2(F2in, NE2p, hoe2);
                 Hd[p] = H;
                 mx = MODE == BULK ? hoe : (half_mask_rt(rb, p) & hoe);
+                if constexpr (DIR) dbits[p] += ext_bits(hoe, hoe2, p);
             } else {
                 // H of the band cells; the virtual row/column cell gets its
                 // exact value and every other slot minus infinity.  The gap
@@ -465,12 +485,14 @@ struct WarpPair16 {
                 F2o[p] = __viaddmax_u16x2(F2in, NE2p, hoe2);
                 Hd[p] = Hm;
                 mx = rm & hoe;
+                if constexpr (DIR) dbits[p] += ext_bits(hoe, hoe2, p);
             }
             // running maximum, two registers per 3-input max
             if (i & 1) lmax = __vimax3_u16x2(lmax, pend, mx);
             else if (i == P - 1) lmax = __vmaxu2(lmax, mx);
             else pend = mx;
         }
+        if constexpr (DIR) return dir_finish<ODD, MODE>(r, lmax, rb, vb, dbits);
         if constexpr (MODE == BULK) {
             // (the band cells of bulk anti-diagonals are counted by run())
             // slots beyond the band sit above every band slot of their lane, so
@@ -501,6 +523,55 @@ struct WarpPair16 {
             if (--until_rebase <= 2) {
                 // slots off the table (past its end, or holding NEG) are
                 // reset; the virtual cells' values are kept
+                if (MODE == TAIL) rebase(last_m, r, rb, table_bits(r - 1));
+                else rebase(last_m, r, rb | vb, table_bits(r - 1) | virtual_bits(r - 1));
+            }
+            return ovf;
+        }
+    }
+
+    // DIR: bits 4-7 of register p's two bytes from the gap states just
+    // written (a state that differs from the opening value extended)
+    __device__ __forceinline__ uint32_t ext_bits(uint32_t hoe, uint32_t hoe2, int p) const {
+        const uint32_t one = 0x10001u;
+        return (__vminu2(Eo[p] ^ hoe, one) << 4) + (__vminu2(Fo[p] ^ hoe, one) << 5) +
+               (__vminu2(E2o[p] ^ hoe2, one) << 6) + (__vminu2(F2o[p] ^ hoe2, one) << 7);
+    }
+
+    // DIR: end of a step.  Store the row, then what the rebase needs: the
+    // anti-diagonal maximum (only when a rebase follows) and the rebase.
+    template <bool ODD, int MODE>
+    __device__ __forceinline__ bool dir_finish(int32_t r, uint32_t lmax, uint32_t rb, uint32_t vb,
+                                               const uint32_t (&db)[P]) {
+        if (r >= 0) {
+            uint32_t wd[C / 4];
+#pragma unroll
+            for (int k = 0; k < C / 4; ++k) wd[k] = prmt(db[2 * k], db[2 * k + 1], 0x6420);
+            uint8_t *p = dtab + (int64_t)r * (32 * C);
+            if constexpr (C % 16 == 0) {
+#pragma unroll
+                for (int k = 0; k < C / 16; ++k)
+                    reinterpret_cast<uint4 *>(p)[k] = make_uint4(wd[4 * k], wd[4 * k + 1], wd[4 * k + 2], wd[4 * k + 3]);
+            } else if constexpr (C % 8 == 0) {
+#pragma unroll
+                for (int k = 0; k < C / 8; ++k) reinterpret_cast<uint2 *>(p)[k] = make_uint2(wd[2 * k], wd[2 * k + 1]);
+            } else {
+                *reinterpret_cast<uint32_t *>(p) = wd[0];
+            }
+        }
+        if constexpr (MODE == BULK) {
+            // fast_pair rebases after the odd step of a pair
+            if (ODD && until_rebase <= 4) {
+                const int32_t lm = (int32_t)max(lmax & 0xffffu, lmax >> 16);
+                last_m = __reduce_max_sync(FULL, lm) + oe;
+            }
+            return false;
+        } else {
+            if (__any_sync(FULL, ovf)) { ovf = true; return true; }
+            if (r < 0) return false;
+            if (--until_rebase <= 2) {
+                const int32_t lm = (int32_t)max(lmax & 0xffffu, lmax >> 16);
+                last_m = __reduce_max_sync(FULL, lm) + oe;
                 if (MODE == TAIL) rebase(last_m, r, rb, table_bits(r - 1));
                 else rebase(last_m, r, rb | vb, table_bits(r - 1) | virtual_bits(r - 1));
             }
@@ -720,6 +791,97 @@ struct WarpPair16 {
             *out = o;
         }
         return true;
+    }
+
+    // DIR: anti-diagonals 0..r_end with their direction bytes in
+    // dt[r * 32C + lane byte]; no termination test.  Returns false if the
+    // scores left the 16-bit range (the int32 kernel then takes the pair).
+    __device__ __forceinline__ bool run_dir(const DevBatch &Bt, int32_t pair, int32_t lane_, int32_t r_end,
+                                            uint8_t *dt) {
+        static_assert(DIR, "run_dir needs the direction variant");
+        prm = Bt.params;
+        lane = lane_;
+        tlen = Bt.t_len[pair]; qlen = Bt.q_len[pair];
+        int32_t tph, qph;
+        {
+            const int64_t toff = Bt.t_off[pair], qoff = Bt.q_off[pair];
+            const int64_t tw0 = toff >> 4, qw0 = qoff >> 4;
+            tp = Bt.t_packed + tw0;
+            qp = Bt.q_packed + qw0;
+            tph = (int32_t)(toff & 15);
+            qph = (int32_t)(qoff & 15);
+            tspan = (int32_t)min(Bt.t_words - tw0, (int64_t)((tph + tlen + 15) >> 4));
+            qspan = (int32_t)min(Bt.q_words - qw0, (int64_t)((qph + qlen + 15) >> 4));
+        }
+        w = effective_w(prm.w, tlen, qlen);
+        oe = prm.q + prm.e; oe2 = prm.q2 + prm.e2;
+        j0 = lane * C;
+        last_r = r_end;
+        dtab = dt + j0;
+        {
+            const int32_t Dp = step_change_max(prm), kint = rebase_interval(Dp);
+            until_rebase = kint;
+            OFF = 0xffff - (kint + 3) * Dp;
+            if (lane == 0) {
+                cold.Dp = Dp;
+                cold.kint = kint;
+                cold.LOWCHK = (int32_t)U_NEG + (kint + 3) * Dp;
+            }
+        }
+        base = 0;
+        last_m = OFF;
+        ovf = false;
+        A2 = ((uint32_t)prm.a & 0xffffu) * 0x10001u;
+        NB2 = ((uint32_t)(-prm.b) & 0xffffu) * 0x10001u;
+        OEp = (uint32_t)oe * 0x10001u;
+        DOEp = (uint32_t)(oe2 - oe) * 0x10001u;
+        Ep = (uint32_t)prm.e * 0x10001u;
+        E2p = (uint32_t)prm.e2 * 0x10001u;
+        NEp = ((uint32_t)(-prm.e) & 0xffffu) * 0x10001u;
+        NE2p = ((uint32_t)(-prm.e2) & 0xffffu) * 0x10001u;
+        NEGp = U_NEG * 0x10001u;
+        L0LO = lane == 0 ? 0x0000ffffu : 0u;
+        L31HI = lane == 31 ? 0xffff0000u : 0u;
+#pragma unroll
+        for (int p = 0; p < P; ++p) {
+            Hev[p] = Hod[p] = Eo[p] = E2o[p] = Fo[p] = F2o[p] = NEGp;
+        }
+        {
+            const int32_t k0 = min(max(w + 1 - j0, 0), C);
+            DF2 = (uint32_t)(k0 - 1) * 0x10001u;
+            if constexpr (DMREG) {
+#pragma unroll
+                for (int p = 0; p < P; ++p)
+                    DMR[p] = prmt(DF2 - ((uint32_t)p | ((uint32_t)(p + P) << 16)), 0, 0xbb99);
+            }
+        }
+        gmax = 0;
+        pend_r = -3;
+        __syncwarp();
+        zdropped = 0;
+        int32_t r = -2;
+        init_windows(r, tph, qph);
+        bool stop = head_step(r);
+        const int32_t head_end = min(last_r, w + 1);
+        while (!stop && r < head_end) {
+            ++r;
+            advance(r);
+            stop = head_step(r);
+        }
+        const int32_t L = min(tlen, qlen);
+        const int32_t bulk_last = min(2 * L - 3 - w, last_r);
+        if (!stop && r == w + 1) {
+            while (r + 2 <= bulk_last) {
+                if (fast_pair(r + 1)) { stop = true; break; }    // only a 16-bit overflow stops it
+                r += 2;
+            }
+        }
+        while (!stop && r < last_r) {
+            ++r;
+            advance(r);
+            stop = tail_step(r);
+        }
+        return !ovf;
     }
 };
 

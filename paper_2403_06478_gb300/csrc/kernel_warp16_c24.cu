@@ -1,11 +1,15 @@
 // Instantiations of the 16-bit packed-lane warp kernel for 24 band slots per
 // lane (w <= 767), at two register budgets (resident blocks per SM): the
 // autotuner picks one per length class.
-#include "kernel_warp16.cuh"
+#include "kernel_tb.cuh"
 
 namespace agatha {
 template cudaError_t launch_warp16_c<24, 3>(const DevBatch *, int, cudaStream_t, int, int);
 template int occupancy_warp16_c<24, 3>();
 template cudaError_t launch_warp16_c<24, 2>(const DevBatch *, int, cudaStream_t, int, int);
 template int occupancy_warp16_c<24, 2>();
+// the traceback variant at one budget (no spills)
+template cudaError_t launch_tb16_c<24, 2>(const DevBatch *, const TbItem *, int32_t, int32_t *, uint8_t *,
+                                          uint32_t *, int32_t *, int, cudaStream_t);
+template int occupancy_tb16_c<24, 2>();
 }  // namespace agatha

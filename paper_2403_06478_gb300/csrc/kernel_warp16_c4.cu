@@ -1,11 +1,15 @@
 // Instantiations of the 16-bit packed-lane warp kernel for 4 band slots per
 // lane (w <= 127), at two register budgets (resident blocks per SM): the
 // autotuner picks one per length class.
-#include "kernel_warp16.cuh"
+#include "kernel_tb.cuh"
 
 namespace agatha {
 template cudaError_t launch_warp16_c<4, 6>(const DevBatch *, int, cudaStream_t, int, int);
 template int occupancy_warp16_c<4, 6>();
 template cudaError_t launch_warp16_c<4, 4>(const DevBatch *, int, cudaStream_t, int, int);
 template int occupancy_warp16_c<4, 4>();
+// the traceback variant at one budget (no spills)
+template cudaError_t launch_tb16_c<4, 6>(const DevBatch *, const TbItem *, int32_t, int32_t *, uint8_t *,
+                                          uint32_t *, int32_t *, int, cudaStream_t);
+template int occupancy_tb16_c<4, 6>();
 }  // namespace agatha

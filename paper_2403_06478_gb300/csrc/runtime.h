@@ -161,4 +161,6 @@ struct agatha_ctx {
     agatha::TbBufs tb;                 // traceback buffers (agatha_align_cigar)
     cudaEvent_t ev_tb0 = nullptr, ev_tb1 = nullptr;
     bool tb_timed = false;
+    float tb_ms = 0.f;                 // traceback kernels of the last call
+    agatha_tb_info tb_info = {0, 0, 0, 0};
 };

@@ -7,9 +7,12 @@
 //    cell become traceback items, ordered by predicted work (anti-diagonals
 //    up to the end x band width), longest first.
 // 3. A direction table takes (r_end + 1) x 32C bytes per pair (C: slots per
-//    lane of the int32 warp kernel for the batch's widest band).  Items run
-//    in waves whose tables fit the device memory this call may use; each wave
-//    is one persistent launch of the traceback kernel (kernel_tb.cuh).
+//    lane of the warp kernel for the batch's widest band).  Items run in
+//    waves whose tables fit the device memory this call may use; each wave
+//    is one persistent launch of a traceback kernel (kernel_tb.cuh): the
+//    16-bit one when the score path may use 16-bit lanes, else (and for the
+//    pairs whose scores leave the 16-bit range, found from the run counts)
+//    the int32 one.
 // 4. The run counts come back to the host, which lays the CIGARs out in
 //    input order; a gather kernel reverses each pair's runs into one dense
 //    device array, copied to the caller's buffer in one transfer.
@@ -64,6 +67,26 @@ int tb_occupancy(int C) {
         case 16: return occupancy_tb_c<16>();
         case 24: return occupancy_tb_c<24>();
         default: return occupancy_tb_c<32>();
+    }
+}
+
+// 16-bit traceback kernel for C16 slots per lane (4, 8, 16 or 24)
+cudaError_t launch_tb16(int C, const DevBatch *d, const TbItem *items, int32_t n, int32_t *head,
+                        uint8_t *dir, uint32_t *ops, int32_t *ncig, int blocks, cudaStream_t s) {
+    switch (C) {
+        case 4: return launch_tb16_c<4, 6>(d, items, n, head, dir, ops, ncig, blocks, s);
+        case 8: return launch_tb16_c<8, 4>(d, items, n, head, dir, ops, ncig, blocks, s);
+        case 16: return launch_tb16_c<16, 3>(d, items, n, head, dir, ops, ncig, blocks, s);
+        default: return launch_tb16_c<24, 2>(d, items, n, head, dir, ops, ncig, blocks, s);
+    }
+}
+
+int tb16_occupancy(int C) {
+    switch (C) {
+        case 4: return occupancy_tb16_c<4, 6>();
+        case 8: return occupancy_tb16_c<8, 4>();
+        case 16: return occupancy_tb16_c<16, 3>();
+        default: return occupancy_tb16_c<24, 2>();
     }
 }
 
@@ -141,10 +164,10 @@ extern "C" int agatha_align_cigar(agatha_ctx *ctx, const agatha_batch *batch, co
     ctx->timed_once = true;
 
     // 2. items, longest predicted work first
-    const int C = pick_slots_per_lane(std::max<int32_t>(shape.max_w_all, 1));
-    const int64_t row = 32 * C;
+    const int C32 = pick_slots_per_lane(std::max<int32_t>(shape.max_w_all, 1));
+    const int C16 = pick_slots16(std::max<int32_t>(shape.max_w_all, 1));
+    const bool use16 = C16 > 0 && step_change_max(p) <= STEP16_MAX && !(flags & AGATHA_FORCE32);
     std::vector<TbItem> items;
-    std::vector<int64_t> cost;
     items.reserve((size_t)n);
     for (int64_t i = 0; i < n; ++i) {
         const int32_t tl = batch->t_len[i], ql = batch->q_len[i];
@@ -173,49 +196,21 @@ extern "C" int agatha_align_cigar(agatha_ctx *ctx, const agatha_batch *batch, co
         for (int64_t k = 0; k < n_items; ++k) sorted[k] = items[ord[k]];
         items.swap(sorted);
     }
-    int64_t ops_total = 0, dir_total = 0, dir_largest = 0;
+    int64_t ops_total = 0;
     for (TbItem &it : items) {
         it.ops_off = ops_total;
         ops_total += (int64_t)it.end_t + it.end_q + 2;
-        const int64_t bytes = ((int64_t)it.end_t + it.end_q + 1) * row;
-        dir_total += bytes;
-        dir_largest = std::max(dir_largest, bytes);
     }
 
-    // 3. buffers and waves
+    // 3. buffers, then waves of the 16-bit kernel and of the int32 kernel
     TbBufs &tb = ctx->tb;
-    if ((rc = ensure_exact(ctx, tb.items, (size_t)std::max<int64_t>(n_items, 1) * sizeof(TbItem))) ||
+    if ((rc = ensure_exact(ctx, tb.items, (size_t)std::max<int64_t>(2 * n_items, 1) * sizeof(TbItem))) ||
         (rc = ensure_exact(ctx, tb.ops, (size_t)std::max<int64_t>(ops_total, 1) * 4)) ||
         (rc = ensure_exact(ctx, tb.n_cigar, (size_t)n * 4)) ||
-        (rc = ensure_exact(ctx, tb.heads, (size_t)std::max<int64_t>(n_items, 1) * 4)) ||
+        (rc = ensure_exact(ctx, tb.heads, (size_t)std::max<int64_t>(2 * n_items, 1) * 4)) ||
         (rc = ensure_exact(ctx, tb.dst_off, (size_t)(n + 1) * 8)))
         return rc;
-    int64_t dir_cap = std::min(dir_total, dir_bytes_available(ctx));
-    if (n_items > 0 && dir_cap < dir_largest)
-        return set_error(ctx, AGATHA_ENOMEM, "a direction table of %lld bytes does not fit in %lld",
-                         (long long)dir_largest, (long long)dir_cap);
-    if (n_items > 0 && (rc = ensure_exact(ctx, tb.dir, (size_t)dir_cap))) return rc;
-    dir_cap = std::max<int64_t>(dir_cap, (int64_t)tb.dir.cap);
-    std::vector<int64_t> wave_begin;
-    {
-        int64_t used = dir_cap;                          // forces a new wave at the first item
-        for (int64_t k = 0; k < n_items; ++k) {
-            const int64_t bytes = ((int64_t)items[k].end_t + items[k].end_q + 1) * row;
-            if (used + bytes > dir_cap) {
-                wave_begin.push_back(k);
-                used = 0;
-            }
-            items[k].dir_off = used;
-            used += bytes;
-        }
-        wave_begin.push_back(n_items);
-    }
-    const int64_t n_waves = (int64_t)wave_begin.size() - 1;
-    if (n_items > 0 &&
-        (e = cudaMemcpyAsync(tb.items.ptr, items.data(), (size_t)n_items * sizeof(TbItem),
-                             cudaMemcpyHostToDevice, s)) != cudaSuccess)
-        return cuda_fail(ctx, e, "copy traceback items");
-    if ((e = cudaMemsetAsync(tb.heads.ptr, 0, (size_t)std::max<int64_t>(n_waves, 1) * 4, s)) ||
+    if ((e = cudaMemsetAsync(tb.heads.ptr, 0, (size_t)std::max<int64_t>(2 * n_items, 1) * 4, s)) ||
         (e = cudaMemsetAsync(tb.n_cigar.ptr, 0, (size_t)n * 4, s)))
         return cuda_fail(ctx, e, "clear traceback counters");
     if (ctx->timing && !ctx->ev_tb0 &&
@@ -223,20 +218,83 @@ extern "C" int agatha_align_cigar(agatha_ctx *ctx, const agatha_batch *batch, co
         cudaGetLastError();
         return set_error(ctx, AGATHA_ECUDA, "traceback timing events");
     }
-    if (ctx->timing && (e = cudaEventRecord(ctx->ev_tb0, s)) != cudaSuccess) return cuda_fail(ctx, e, "event");
-    const int resident = ctx->n_sm * tb_occupancy(C);
-    const TbItem *d_items = (const TbItem *)tb.items.ptr;
-    for (int64_t wv = 0; wv < n_waves; ++wv) {
-        const int64_t b = wave_begin[wv], cnt = wave_begin[wv + 1] - b;
-        const int blocks = (int)std::max<int64_t>(1, std::min<int64_t>(resident, (cnt + 3) / 4));
-        e = launch_tb(C, ctx->main.d_desc, d_items + b, (int32_t)cnt, (int32_t *)tb.heads.ptr + wv,
-                      (uint8_t *)tb.dir.ptr, (uint32_t *)tb.ops.ptr, (int32_t *)tb.n_cigar.ptr, blocks, s);
-        if (e != cudaSuccess) return cuda_fail(ctx, e, "traceback launch");
+    ctx->tb_ms = 0.f;
+    int64_t item_base = 0, head_base = 0;     // where this kind's items / queue heads start
+    // one kind of kernel over `list`: waves whose tables fit, each one launch
+    auto run_kind = [&](std::vector<TbItem> &list, bool packed) -> int {
+        if (list.empty()) return AGATHA_OK;
+        const int C = packed ? C16 : C32;
+        const int64_t row = 32 * C;
+        int64_t total = 0, largest = 0;
+        for (const TbItem &it : list) {
+            const int64_t bytes = ((int64_t)it.end_t + it.end_q + 1) * row;
+            total += bytes;
+            largest = std::max(largest, bytes);
+        }
+        int64_t cap = std::min(total, dir_bytes_available(ctx));
+        if (cap < largest)
+            return set_error(ctx, AGATHA_ENOMEM, "a direction table of %lld bytes does not fit in %lld",
+                             (long long)largest, (long long)cap);
+        int r2 = ensure_exact(ctx, tb.dir, (size_t)cap);
+        if (r2) return r2;
+        cap = std::max<int64_t>(cap, (int64_t)tb.dir.cap);
+        std::vector<int64_t> begin;
+        int64_t used = cap;                      // forces a new wave at the first item
+        for (size_t k = 0; k < list.size(); ++k) {
+            const int64_t bytes = ((int64_t)list[k].end_t + list[k].end_q + 1) * row;
+            if (used + bytes > cap) {
+                begin.push_back((int64_t)k);
+                used = 0;
+            }
+            list[k].dir_off = used;
+            used += bytes;
+        }
+        begin.push_back((int64_t)list.size());
+        TbItem *d_items = (TbItem *)tb.items.ptr + item_base;
+        cudaError_t e2 = cudaMemcpyAsync(d_items, list.data(), list.size() * sizeof(TbItem),
+                                         cudaMemcpyHostToDevice, s);
+        if (e2 != cudaSuccess) return cuda_fail(ctx, e2, "copy traceback items");
+        if (ctx->timing && (e2 = cudaEventRecord(ctx->ev_tb0, s)) != cudaSuccess) return cuda_fail(ctx, e2, "event");
+        const int resident = ctx->n_sm * (packed ? tb16_occupancy(C) : tb_occupancy(C));
+        for (size_t wv = 0; wv + 1 < begin.size(); ++wv) {
+            const int64_t b = begin[wv], cnt = begin[wv + 1] - b;
+            const int blocks = (int)std::max<int64_t>(1, std::min<int64_t>(resident, (cnt + 3) / 4));
+            int32_t *head = (int32_t *)tb.heads.ptr + head_base + (int64_t)wv;
+            e2 = packed ? launch_tb16(C, ctx->main.d_desc, d_items + b, (int32_t)cnt, head, (uint8_t *)tb.dir.ptr,
+                                      (uint32_t *)tb.ops.ptr, (int32_t *)tb.n_cigar.ptr, blocks, s)
+                        : launch_tb(C, ctx->main.d_desc, d_items + b, (int32_t)cnt, head, (uint8_t *)tb.dir.ptr,
+                                    (uint32_t *)tb.ops.ptr, (int32_t *)tb.n_cigar.ptr, blocks, s);
+            if (e2 != cudaSuccess) return cuda_fail(ctx, e2, "traceback launch");
+        }
+        if (ctx->timing && (e2 = cudaEventRecord(ctx->ev_tb1, s)) != cudaSuccess) return cuda_fail(ctx, e2, "event");
+        if ((e2 = cudaStreamSynchronize(s)) != cudaSuccess) return cuda_fail(ctx, e2, "traceback");
+        if (ctx->timing) {
+            float ms = 0.f;
+            if ((e2 = cudaEventElapsedTime(&ms, ctx->ev_tb0, ctx->ev_tb1)) != cudaSuccess)
+                return cuda_fail(ctx, e2, "traceback timing");
+            ctx->tb_ms += ms;
+        }
+        item_base += (int64_t)list.size();
+        head_base += (int64_t)begin.size() - 1;
+        (packed ? ctx->tb_info.pairs16 : ctx->tb_info.pairs32) += (int64_t)list.size();
+        ctx->tb_info.waves += (int64_t)begin.size() - 1;
+        return AGATHA_OK;
+    };
+    ctx->tb_info = agatha_tb_info{0, 0, 0, 0};
+    std::vector<int32_t> ncig((size_t)n);
+    std::vector<TbItem> rest;
+    if (use16) {
+        if ((rc = run_kind(items, true))) return rc;
+        if ((e = cudaMemcpy(ncig.data(), tb.n_cigar.ptr, (size_t)n * 4, cudaMemcpyDeviceToHost)))
+            return cuda_fail(ctx, e, "traceback run counts");
+        for (const TbItem &it : items)
+            if (ncig[it.pair] < 0) rest.push_back(it);      // scores left the 16-bit range
+    } else {
+        rest = items;
     }
-    if (ctx->timing && (e = cudaEventRecord(ctx->ev_tb1, s)) != cudaSuccess) return cuda_fail(ctx, e, "event");
+    if ((rc = run_kind(rest, false))) return rc;
 
     // 4. layout in input order, gather, copy back
-    std::vector<int32_t> ncig((size_t)n);
     if ((e = cudaMemcpyAsync(ncig.data(), tb.n_cigar.ptr, (size_t)n * 4, cudaMemcpyDeviceToHost, s)) ||
         (e = cudaStreamSynchronize(s)))
         return cuda_fail(ctx, e, "traceback run counts");
@@ -250,6 +308,9 @@ extern "C" int agatha_align_cigar(agatha_ctx *ctx, const agatha_batch *batch, co
     if ((rc = ensure_exact(ctx, tb.dense, (size_t)total * 4))) return rc;
     if ((e = cudaMemcpyAsync(tb.dst_off.ptr, cigar_off, (size_t)(n + 1) * 8, cudaMemcpyHostToDevice, s)))
         return cuda_fail(ctx, e, "copy CIGAR offsets");
+    // the gather walks the 16-bit kernel's items: every item (its n_cigar
+    // is final now), or the int32 list when the 16-bit kernel did not run
+    const TbItem *d_items = (const TbItem *)tb.items.ptr;
     const int gblocks = (int)std::max<int64_t>(1, std::min<int64_t>((int64_t)ctx->n_sm * 8, (n_items + 7) / 8));
     if ((e = launch_cigar_gather(d_items, (int32_t)n_items, (const int32_t *)tb.n_cigar.ptr,
                                  (const int64_t *)tb.dst_off.ptr, (const uint32_t *)tb.ops.ptr,
@@ -261,11 +322,17 @@ extern "C" int agatha_align_cigar(agatha_ctx *ctx, const agatha_batch *batch, co
     return AGATHA_OK;
 }
 
+extern "C" int agatha_last_traceback_info(agatha_ctx *ctx, agatha_tb_info *info) {
+    if (!ctx || !info) return AGATHA_EINVAL;
+    std::lock_guard<std::mutex> lock(ctx->mu);
+    *info = ctx->tb_info;
+    return AGATHA_OK;
+}
+
 extern "C" int agatha_last_traceback_ms(agatha_ctx *ctx, float *ms) {
     if (!ctx || !ms) return AGATHA_EINVAL;
     if (!ctx->timing) return AGATHA_ENOTSUP;
     if (!ctx->tb_timed) return AGATHA_EAGAIN;
-    cudaError_t e = cudaEventSynchronize(ctx->ev_tb1);
-    if (e == cudaSuccess) e = cudaEventElapsedTime(ms, ctx->ev_tb0, ctx->ev_tb1);
-    return e == cudaSuccess ? AGATHA_OK : cuda_fail(ctx, e, "traceback timing");
+    *ms = ctx->tb_ms;
+    return AGATHA_OK;
 }

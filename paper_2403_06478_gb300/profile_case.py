@@ -22,8 +22,10 @@ def main():
     ap.add_argument("--workload", default="ont")
     ap.add_argument("--pairs", type=int, default=2000)
     ap.add_argument("--repeat", type=int, default=2)
-    ap.add_argument("--length", type=int, default=20000, help="pair length of --workload identical")
+    ap.add_argument("--length", type=int, default=20000,
+                    help="pair length of --workload identical / fixed")
     ap.add_argument("--path", default="batched", choices=sorted(FLAGS))
+    ap.add_argument("--traceback", action="store_true", help="agatha_align_cigar instead")
     args = ap.parse_args()
     B.build()
     if args.workload == "identical":
@@ -32,12 +34,18 @@ def main():
         rng = np.random.default_rng(5)
         xs = [rng.integers(0, 4, args.length).astype(np.uint8) for _ in range(args.pairs)]
         batch = W.from_pairs(xs, [x.copy() for x in xs], W.ONT_SCORING, name="identical")
+    elif args.workload == "fixed":
+        # pairs of one length with small-config errors and ONT-like scoring
+        batch = W.make_long_ratio(1.0, n_pairs=args.pairs, long_len=args.length)
     else:
         batch = W.make_config(args.workload, n_pairs=args.pairs)
     pb = A.pack_batch(batch)
     with A.Context(0) as ctx:
         for _ in range(args.repeat):
-            res = ctx.align_host(pb, batch.scoring, flags=FLAGS[args.path])
+            if args.traceback:
+                res, off, _ = ctx.align_cigar(pb, batch.scoring, flags=FLAGS[args.path])
+            else:
+                res = ctx.align_host(pb, batch.scoring, flags=FLAGS[args.path])
     print(f"ok {args.workload} pairs={batch.n_pairs} cells={int(res['cells'].sum())}")
 
 

@@ -78,9 +78,24 @@ def _check(ctx, batch, label, idx=None, flags=0):
     return res, off, cig
 
 
+def _kernels(ctx, res, batch, packed):
+    """The traceback kernel that ran: every traced pair on 16-bit lanes (none
+    handed back) or every one on int32 lanes."""
+    info = ctx.last_traceback_info()
+    et, _ = _end_cells(res, batch)
+    traced = int((et >= 0).sum())
+    if packed:
+        assert info["pairs16"] == traced and info["pairs32"] == 0, info
+    else:
+        assert info["pairs16"] == 0 and info["pairs32"] == traced, info
+    assert info["waves"] >= (1 if traced else 0)
+
+
 @pytest.mark.parametrize("flags", [0, A.AGATHA_PLAIN, A.AGATHA_FORCE32])
 def test_small_config_every_pair(ctx, flags):
-    _check(ctx, W.make_config("small"), f"small/{flags}", flags=flags)
+    batch = W.make_config("small")
+    res, _, _ = _check(ctx, batch, f"small/{flags}", flags=flags)
+    _kernels(ctx, res, batch, packed=not flags & A.AGATHA_FORCE32)
     assert ctx.last_traceback_ms() > 0
 
 
@@ -88,12 +103,40 @@ def test_small_config_every_pair(ctx, flags):
 def test_adversarial_pairs(ctx, si):
     scoring = ADVERSARIAL_SCORINGS[si]
     batch = _adversarial_batch(np.random.default_rng(100 + si), scoring)
-    _check(ctx, batch, f"adversarial[{si}]")
+    for flags in (0, A.AGATHA_FORCE32):
+        _check(ctx, batch, f"adversarial[{si}]/{flags}", flags=flags)
 
 
 @pytest.mark.parametrize("name,n", [("ont", 120), ("hifi", 120), ("skewed", 600)])
-def test_workload_mixes_every_pair(ctx, name, n):
-    _check(ctx, W.make_config(name, n_pairs=n), name)
+@pytest.mark.parametrize("flags", [0, A.AGATHA_FORCE32])
+def test_workload_mixes_every_pair(ctx, name, n, flags):
+    batch = W.make_config(name, n_pairs=n)
+    res, _, _ = _check(ctx, batch, f"{name}/{flags}", flags=flags)
+    _kernels(ctx, res, batch, packed=not flags)
+
+
+def test_16bit_overflow_hands_pairs_to_int32(ctx):
+    # pairs whose band spreads scores beyond what 16-bit lanes keep (as in the
+    # score path's overflow test): the 16-bit traceback kernel hands them back
+    # and the int32 kernel traces them; the short ones stay on 16-bit lanes
+    rng = np.random.default_rng(17)
+    scoring = W.Scoring(64, 64, 1, 63, 1, 63, 511, -1, 0)
+    qs, ts = [], []
+    for k in range(4):
+        x = rng.integers(0, 4, 2500 + 100 * k).astype(np.uint8)
+        y = x.copy()
+        y[rng.integers(0, x.size, 20)] = rng.integers(0, 4, 20)
+        qs.append(x)
+        ts.append(y)
+    for k in range(5):
+        x = rng.integers(0, 4, 250).astype(np.uint8)
+        qs.append(x)
+        ts.append(x.copy())
+    batch = W.from_pairs(qs, ts, scoring)
+    res, _, _ = _check(ctx, batch, "overflow")
+    assert (res["lane16"][:4] == 0).all()           # the score path recomputed them too
+    info = ctx.last_traceback_info()
+    assert info["pairs16"] == 9 and 1 <= info["pairs32"] <= 4, info
 
 
 @pytest.mark.parametrize("scoring", [
@@ -113,7 +156,9 @@ def test_steep_and_tied_scorings(ctx, scoring):
             cut = int(rng.integers(0, min(scoring.w, L // 2)))
             qs.append(x)
             ts.append(y[: L - cut] if k % 2 else np.concatenate([y, rng.integers(0, 4, cut)]).astype(np.uint8))
-    _check(ctx, W.from_pairs(qs, ts, scoring), f"steep/{scoring}")
+    batch = W.from_pairs(qs, ts, scoring)
+    for flags in (0, A.AGATHA_FORCE32):
+        _check(ctx, batch, f"steep/{scoring}/{flags}", flags=flags)
 
 
 def test_empty_and_degenerate_pairs(ctx):
@@ -165,4 +210,5 @@ def test_ont_full_size_sampled(ctx):
     rng = np.random.default_rng(11)
     longest = np.argsort(-(batch.q_len.astype(np.int64) + batch.t_len))[:6]
     idx = np.unique(np.concatenate([longest, rng.choice(batch.n_pairs, 40, replace=False)]))
-    _check(ctx, batch, "ont/full", idx=idx)
+    res, _, _ = _check(ctx, batch, "ont/full", idx=idx)
+    _kernels(ctx, res, batch, packed=True)
