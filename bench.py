@@ -58,9 +58,10 @@ L2_FLUSH_BYTES = 512 << 20          # > 129 MB of L2
 # 16x2 lane op serves two cells
 OPS_PER_CELL_I32 = 13.0
 OPS_PER_CELL_I16X2 = 6.5
-# traceback kernel: the int32 cell ops plus the direction byte (H source:
-# four compare-selects; four gap-continuation compares; one byte insert)
+# traceback kernel: the cell ops plus the direction byte (four equality and
+# four gap-continuation comparisons, one byte insert); halved on 16x2 lanes
 OPS_PER_CELL_TB = OPS_PER_CELL_I32 + 9.0
+OPS_PER_CELL_TB16 = OPS_PER_CELL_TB / 2
 CPU_SAMPLE_PAIRS = 6000
 CPU_SAMPLE_CELLS = 4e10             # about 12 s of the oracle on 16 cores
 REF_STEP_PAIRS = 300
@@ -146,13 +147,27 @@ def traffic_from_profile(kernel):
     return d.get("dram_bytes_per_launch")
 
 
-def _kernel_digest():
+def traffic_tb16(kernel, table_bytes):
+    """DRAM bytes of one traceback launch, scaled from the committed capture
+    of a smaller case by direction-table bytes (null for another build)."""
+    path = os.path.join(ROOT, "profiles", "tb16_kernel_traffic.json")
+    if not os.path.exists(path):
+        return None
+    with open(path) as fh:
+        d = json.load(fh)
+    if d.get("kernel") != kernel or d.get("kernel_digest") != _kernel_digest(
+            ("kernel_tb.cuh", "kernel_warp16.cuh", "kernel_warp16_c16.cu", "agatha_dev.cuh")):
+        return None
+    return int(d["dram_bytes_per_table_byte"] * table_bytes)
+
+
+def _kernel_digest(files=None):
     """Digest of the 16-bit kernel's sources: a traffic figure is only valid
     for the build it was measured on."""
     import hashlib
     h = hashlib.sha256()
-    for f in ("kernel_warp16.cuh", "kernel_warp16_c4.cu", "kernel_warp16_c8.cu", "kernel_warp16_c16.cu",
-              "kernel_warp16_c24.cu", "agatha_dev.cuh"):
+    for f in files or ("kernel_warp16.cuh", "kernel_warp16_c4.cu", "kernel_warp16_c8.cu",
+                       "kernel_warp16_c16.cu", "kernel_warp16_c24.cu", "agatha_dev.cuh"):
         with open(os.path.join(ROOT, "paper_2403_06478_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
@@ -262,7 +277,6 @@ def run_traceback(args):
     stream = torch.cuda.Stream()
     torch.cuda.set_stream(stream)
     flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device="cuda")
-    free0, total0 = torch.cuda.mem_get_info(local)
     ctx = A.Context(local, timing=True, autotune=True, tune_cache_path=args.tune_cache)
     ctx.align_host(pb, batch.scoring)                     # autotune the score path
     for _ in range(args.warmup):
@@ -290,9 +304,17 @@ def run_traceback(args):
     sm_max_mhz = float(peaks.get("sm_max_mhz", 2070.0))
     int_peak = n_sm * 128 * sm_max_mhz * 1e6 / 1e12
     t_ms = statistics.mean(tb_ms)
-    achieved = tcells * OPS_PER_CELL_TB / (t_ms / 1e3) / 1e12
+    info = ctx.last_traceback_info()
+    packed = info["pairs16"] > 0 and info["pairs32"] * 2 < info["pairs16"]
+    ops_cell = OPS_PER_CELL_TB16 if packed else OPS_PER_CELL_TB
+    achieved = tcells * ops_cell / (t_ms / 1e3) / 1e12
     w = batch.scoring.w
-    C = next(c for c in (4, 8, 16, 24, 32) if 32 * c - 1 >= w)
+    if packed:
+        C = next(c for c in (4, 8, 16, 24) if 32 * c - 1 >= w)
+        kernel = f"tb16_kernel<{C}, {dict([(4, 6), (8, 4), (16, 3), (24, 2)])[C]}>"
+    else:
+        C = next(c for c in (4, 8, 16, 24, 32) if 32 * c - 1 >= w)
+        kernel = f"tb_kernel<{C}>"
     table_bytes = sum(((int(r["mqe_t"]) + int(batch.q_len[i]) - 1) if r["reach_end"] else
                        (int(r["te"]) + int(r["qe"]))) + 1 for i, r in enumerate(res)
                       if batch.t_len[i] > 0 and batch.q_len[i] > 0 and
@@ -301,7 +323,8 @@ def run_traceback(args):
         "metric": "GCUPS with traceback (score path + CIGAR of every extension), bit-exact",
         "value": round(cells / (k_ms / 1e3) / 1e9, 3), "unit": "GCUPS", "n_gpus": 1,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(k_ms, 3),
-        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int32",
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "int16x2" if packed else "int32",
         "data": "synthetic",
         "config": {"workload": WORKLOADS[args.workload], "pairs_per_gpu": n, "cells_per_step": cells,
                    "traceback_cells_per_step": tcells, "cigar_runs_per_step": int(off[-1]),
@@ -317,14 +340,14 @@ def run_traceback(args):
                 "d2h_bytes_per_step": int(n * 48 + 4 * n + 4 * int(off[-1])),
                 "ms_per_step": round(statistics.mean(wall_ms), 3)},
         # score path (prep 3, 16-bit kernel, overflow kernel), one traceback
-        # launch per wave (tables up to the free memory less min(1/16, 4 GiB)),
-        # the CIGAR gather
-        "gpu_launches": args.steps * (5 + -(-table_bytes // max(1, free0 - min(total0 // 16, 4 << 30)
-                                                             - (1 << 30))) + 1),
+        # launch per wave, the CIGAR gather
+        "gpu_launches": args.steps * (5 + info["waves"] + 1),
+        "traceback_pairs": {"lanes16": info["pairs16"], "int32": info["pairs32"], "waves": info["waves"]},
         "roofline": {"bound": "alu", "achieved": round(achieved, 3), "peak": round(int_peak, 3),
-                     "unit": "Tops/s", "frac": round(achieved / int_peak, 4), "traffic": None,
-                     "kernel": f"tb_kernel<{C}>", "kernel_ms": round(t_ms, 3),
-                     "ops_per_cell": OPS_PER_CELL_TB,
+                     "unit": "Tops/s", "frac": round(achieved / int_peak, 4),
+                     "traffic": traffic_tb16(kernel, table_bytes) if packed else None,
+                     "kernel": kernel, "kernel_ms": round(t_ms, 3),
+                     "ops_per_cell": ops_cell,
                      "peak_basis": f"{n_sm} SMs x 128 int32 lanes x {sm_max_mhz:.0f} MHz ({peak_kind})"},
         "clocks": clocks,
     }
