@@ -64,6 +64,7 @@ OPS_PER_CELL_TB = OPS_PER_CELL_I32 + 9.0
 OPS_PER_CELL_TB16 = OPS_PER_CELL_TB / 2
 CPU_SAMPLE_PAIRS = 6000
 CPU_SAMPLE_CELLS = 4e10             # about 12 s of the oracle on 16 cores
+CPU_SAMPLE_CELLS_1T = 2e9           # about 10 s on one core
 REF_STEP_PAIRS = 300
 
 
@@ -187,8 +188,17 @@ def cpu_baseline(batch, n_sample: int, seed: int = 7):
     res = O.align_batch(batch, idx=idx, threads=cores)
     dt = time.perf_counter() - t0
     cells = int(res["cells"].sum())
+    # one thread on a smaller part of the same sample (about 10 s)
+    est1 = np.cumsum(S.predicted_cells(batch.q_len[idx], batch.t_len[idx], batch.scoring.w))
+    one = idx[:max(1, int(np.searchsorted(est1, CPU_SAMPLE_CELLS_1T)) + 1)]
+    t0 = time.perf_counter()
+    res1 = O.align_batch(batch, idx=one, threads=1)
+    dt1 = time.perf_counter() - t0
+    cells1 = int(res1["cells"].sum())
     return {"value": round(cells / dt / 1e9, 4), "unit": "GCUPS", "cores": cores, "kind": "oracle",
-            "sample": f"{idx.size} seeded random pairs of the workload ({cells} cells, {dt:.1f} s)"}
+            "sample": f"{idx.size} seeded random pairs of the workload ({cells} cells, {dt:.1f} s)",
+            "single_thread": {"value": round(cells1 / dt1 / 1e9, 4), "unit": "GCUPS", "cores": 1,
+                              "sample": f"{one.size} of those pairs ({cells1} cells, {dt1:.1f} s)"}}
 
 
 def run_reference(args):
