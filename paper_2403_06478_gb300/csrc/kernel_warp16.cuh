@@ -146,6 +146,7 @@ struct WarpPair16 {
     bool ovf;
     // packed constants
     uint32_t A2, NB2, OEp, DOEp, Ep, E2p, NEp, NE2p, NEGp, L0LO, L31HI;
+    uint32_t NABs;                 // -(a + b) as a 32-bit multiplier of the mismatch bits
     // bookkeeping (uniform across the warp)
     int32_t gmax;
     int32_t zdropped;
@@ -439,17 +440,29 @@ struct WarpPair16 {
                 Fin = p < P - 1 ? Fo[p + 1] : edge;
                 F2in = p < P - 1 ? F2o[p + 1] : edge2;
             }
-            // substitution: mismatch bits of both halves replicated to 0xFFFF masks
-            const uint32_t mm = mismatch_mask(comb, p);
-            const uint32_t s2 = mux(mm, NB2, A2);
+            // substitution: H(r-2) + s = (H(r-2) - m (a+b)) + a per half, m = 1
+            // where the bases differ.  The first part is one multiply-add of
+            // the mismatch bits: no half borrows, since every score a later
+            // cell of the table can read stays far above a + b (the same
+            // argument as for the open terms below).  C = 24 keeps its
+            // bits in two words and uses the replicated-mask form.
+            uint32_t Hs, s2;
+            if constexpr (C <= 16) {
+                const uint32_t mb = (comb.lo >> (2 * p)) & 0x10001u;
+                Hs = mb * NABs + Hd[p];
+                s2 = A2;
+            } else {
+                Hs = Hd[p];
+                s2 = mux(mismatch_mask(comb, p), NB2, A2);
+            }
             // H = max(H(r-2) + s, E, F, E2, F2): add-max, 3-input max, max
-            const uint32_t H = __vmaxu2(__vimax3_u16x2(__viaddmax_u16x2(Hd[p], s2, Ein), Fin, E2in),
+            const uint32_t H = __vmaxu2(__vimax3_u16x2(__viaddmax_u16x2(Hs, s2, Ein), Fin, E2in),
                                         F2in);
             if constexpr (DIR) {
                 // 1 per half where H differs from the input (scores sit far
                 // above 0, so the per-half add of s needs no further clamp)
                 const uint32_t one = 0x10001u;
-                const uint32_t hd = __viaddmax_u16x2(Hd[p], s2, 0u);
+                const uint32_t hd = __viaddmax_u16x2(Hs, s2, 0u);
                 dbits[p] = __vminu2(H ^ hd, one) + (__vminu2(H ^ Ein, one) << 1) +
                            (__vminu2(H ^ Fin, one) << 2) + (__vminu2(H ^ E2in, one) << 3);
             }
@@ -708,6 +721,7 @@ struct WarpPair16 {
         ovf = false;
         A2 = ((uint32_t)prm.a & 0xffffu) * 0x10001u;
         NB2 = ((uint32_t)(-prm.b) & 0xffffu) * 0x10001u;
+        NABs = 0u - (uint32_t)(prm.a + prm.b);
         OEp = (uint32_t)oe * 0x10001u;
         DOEp = (uint32_t)(oe2 - oe) * 0x10001u;
         Ep = (uint32_t)prm.e * 0x10001u;
@@ -833,6 +847,7 @@ struct WarpPair16 {
         ovf = false;
         A2 = ((uint32_t)prm.a & 0xffffu) * 0x10001u;
         NB2 = ((uint32_t)(-prm.b) & 0xffffu) * 0x10001u;
+        NABs = 0u - (uint32_t)(prm.a + prm.b);
         OEp = (uint32_t)oe * 0x10001u;
         DOEp = (uint32_t)(oe2 - oe) * 0x10001u;
         Ep = (uint32_t)prm.e * 0x10001u;
