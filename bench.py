@@ -135,9 +135,11 @@ def measured_peaks():
     return {"hbm_gbs": 6800.0, "sm_max_mhz": 2070.0}, "fallback"
 
 
-def traffic_from_profile(kernel):
-    """DRAM bytes per full-size launch of the dominant kernel, from the
-    committed ncu summary (null if it was taken on another kernel build)."""
+def traffic_from_profile(kernel, input_bytes):
+    """DRAM bytes per launch of the dominant kernel, from the committed ncu
+    capture of a smaller case of the same kernel scaled by input bytes (the
+    kernel reads its inputs once; band state never leaves the SM); null if
+    the capture was taken on another kernel or build."""
     path = os.path.join(ROOT, "profiles", "warp16_kernel_ont_traffic.json")
     if not os.path.exists(path):
         return None
@@ -145,7 +147,7 @@ def traffic_from_profile(kernel):
         d = json.load(fh)
     if d.get("kernel") != kernel or d.get("kernel_digest") != _kernel_digest():
         return None
-    return d.get("dram_bytes_per_launch")
+    return int(d["dram_bytes_per_input_byte"] * input_bytes)
 
 
 def traffic_tb16(kernel, table_bytes):
@@ -536,7 +538,7 @@ def main():
         "gpu_launches": launches_per_step * args.steps,
         "roofline": {"bound": "alu", "achieved": round(achieved, 3),
                      "peak": round(int_peak, 3), "unit": "Tops/s", "frac": round(achieved / int_peak, 4),
-                     "traffic": traffic_from_profile(kernel), "kernel": kernel,
+                     "traffic": traffic_from_profile(kernel, h2d), "kernel": kernel,
                      "kernel_ms": round(k_ms, 3), "ops_per_cell": round(ops / max(cells, 1), 3),
                      "peak_basis": f"{n_sm} SMs x 128 int32 lanes x {sm_max_mhz:.0f} MHz ({peak_kind})"},
         "clocks": clocks,

@@ -193,7 +193,8 @@ int64_t agatha_band_cells(int32_t tlen, int32_t qlen, int32_t w);
  * budget, 2: int32 lanes).  The batch (up to 131072 of its pairs) is then
  * timed as one launch of each 16-bit variant (and of int32 lanes if a class
  * preferred them) and, if the classes disagree, with one launch per class.  The fastest plan
- * is kept (anything but one launch of variant 0 must win by 2%), per context
+ * is kept (anything but one launch of variant 0 must win by 2% on a class's
+ * sample and by 1% on the batch), per context
  * and in tune_cache_path (one line per key, read at agatha_init).  Every
  * variant gives bit-identical results.  agatha_tune_variants writes what was
  * tuned for `params` (band half-width w_max: the widest effective band of

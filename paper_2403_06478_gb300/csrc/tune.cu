@@ -7,11 +7,12 @@
 // chosen per length class, by measurement, the first time a host batch
 // arrives for a scoring and band width: the pairs of each class (up to 4096,
 // spread over the class) are aligned with every variant and the fastest one
-// kept (a variant other than the default must win by 2%).  The batch itself
-// (up to 131072 of its pairs) is then timed as one launch of each 16-bit
-// variant (and of int32 lanes if a class preferred them) and, if the classes
-// disagree, as one launch per class; the fastest plan is kept (again with a
-// 2% margin for anything but one launch of the default variant).
+// kept (a variant other than the default must win by 2% on these samples).
+// The batch itself (up to 131072 of its pairs) is then timed as one launch of
+// each 16-bit variant (and of int32 lanes if a class preferred them) and, if
+// the classes disagree, as one launch per class; the fastest plan is kept
+// (with a 1% margin, on the whole batch, for anything but one launch of the
+// default variant).
 // Every variant computes the same exact results, so the choice only moves
 // time.  Choices are kept per context and, with a cache path, in a text file
 // (one line per key: the key, the four class variants and the split flag).
@@ -100,8 +101,10 @@ struct SubBatch {
     }
 };
 
-// A variant other than the default must win by this much to be taken.
+// A variant other than the default must win by this much to be taken: on a
+// class's sample, and on the whole batch (repeatable to well under 1%).
 constexpr float kMargin = 0.98f;
+constexpr float kMarginBatch = 0.99f;
 
 int tune_run(agatha_ctx *ctx, const agatha_batch *b, const DevParams &p, uint32_t flags, cudaStream_t s,
              const LaunchPlan &lp, TuneChoice *choice) {
@@ -155,7 +158,7 @@ int tune_run(agatha_ctx *ctx, const agatha_batch *b, const DevParams &p, uint32_
         const int rc = time_plan(ctx, whole.b, p, flags, s, single_variant(lp, v), res, &t);
         if (rc) return rc;
         if (v == VAR_16) best = t;
-        else if (t < kMargin * best) { best = t; best_v = v; }
+        else if (t < kMarginBatch * best) { best = t; best_v = v; }
     }
     for (int c = 0; c < N_CLASSES; ++c) choice->var[c] = (int8_t)best_v;
     bool mixed = false;
@@ -168,7 +171,7 @@ int tune_run(agatha_ctx *ctx, const agatha_batch *b, const DevParams &p, uint32_
         float t_split = 0.f;
         const int rc = time_plan(ctx, whole.b, p, flags, s, split, res, &t_split);
         if (rc) return rc;
-        if (t_split < kMargin * best) {
+        if (t_split < kMarginBatch * best) {
             *choice = per;
             choice->split = 1;
         }
