@@ -272,13 +272,20 @@ def run_traceback(args):
 
     value = score cells / (score kernels + traceback kernels), CUDA events on
     the call's stream; e2e = the same cells / the whole call (copies both
-    ways, host planning between the passes), both from pinned host buffers."""
+    ways, host planning between the passes), both from pinned host buffers.
+    Under torchrun each rank traces its own batch (weak scaling); rank 0
+    prints the units of all ranks over the slowest rank's time."""
     import torch
     from paper_2403_06478_gb300 import agatha as A
     from paper_2403_06478_gb300 import build as B
+    from paper_2403_06478_gb300 import shard as S
     from paper_2403_06478_gb300 import workload as W
     rank, world, local = _env_int("RANK", 0), _env_int("WORLD_SIZE", 1), _env_int("LOCAL_RANK", 0)
     torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     B.build()
     batch = W.make_config(args.workload, seed=None if rank == 0 else W.SEED_BASE + 2 + 1000 * rank)
     pb = A.pack_batch(batch)
@@ -293,6 +300,10 @@ def run_traceback(args):
     ctx.align_host(pb, batch.scoring)                     # autotune the score path
     for _ in range(args.warmup):
         res, off, cig = ctx.align_cigar(pin_pb, batch.scoring, stream=stream.cuda_stream)
+    torch.cuda.synchronize()
+    if dist is not None:
+        dist.barrier()
+    torch.cuda.synchronize()
     sampler = ClockSampler(local)
     sampler.start()
     wall_ms, score_ms, tb_ms = [], [], []
@@ -304,13 +315,20 @@ def run_traceback(args):
         wall_ms.append((time.perf_counter() - t0) * 1e3)
         score_ms.append(ctx.last_kernel_ms())
         tb_ms.append(ctx.last_traceback_ms())
+    torch.cuda.synchronize()
     clocks = sampler.stop()
     alone = A.agatha_align_batch(ctx, batch)
     exact = bool(A.results_equal(res, alone).size == 0)
     cells = int(res["cells"].sum())
+    (all_cells, all_pairs), (k_tot, wall_tot) = S.reduce_step_stats(
+        [cells, pb.n_pairs], [sum(score_ms) + sum(tb_ms), sum(wall_ms)], device="cuda")
+    if rank != 0:
+        ctx.close()
+        if dist is not None:
+            dist.destroy_process_group()
+        return 0
     tcells = traceback_cells(res, batch)
     n = pb.n_pairs
-    k_ms = statistics.mean(score_ms) + statistics.mean(tb_ms)
     peaks, peak_kind = measured_peaks()
     n_sm = torch.cuda.get_device_properties(local).multi_processor_count
     sm_max_mhz = float(peaks.get("sm_max_mhz", 2070.0))
@@ -333,8 +351,8 @@ def run_traceback(args):
                       (r["reach_end"] or r["te"] >= 0)) * 32 * C
     line = {
         "metric": "GCUPS with traceback (score path + CIGAR of every extension), bit-exact",
-        "value": round(cells / (k_ms / 1e3) / 1e9, 3), "unit": "GCUPS", "n_gpus": 1,
-        "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(k_ms, 3),
+        "value": round(all_cells * args.steps / (k_tot / 1e3) / 1e9, 3), "unit": "GCUPS", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(k_tot / args.steps, 3),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "int16x2" if packed else "int32",
         "data": "synthetic",
@@ -343,14 +361,14 @@ def run_traceback(args):
                    "direction_table_bytes": int(table_bytes),
                    "l2": "flushed between steps (512 MB write)",
                    "value_basis": "score kernels + traceback kernels, CUDA events"},
-        "pairs_per_s": round(n / (k_ms / 1e3), 1),
+        "pairs_per_s": round(all_pairs * args.steps / (k_tot / 1e3), 1),
         "score_kernel_ms": round(statistics.mean(score_ms), 3),
         "traceback_kernel_ms": round(t_ms, 3),
         "results_equal_score_path": exact,
-        "e2e": {"value": round(cells / (statistics.mean(wall_ms) / 1e3) / 1e9, 3), "unit": "GCUPS",
+        "e2e": {"value": round(all_cells * args.steps / (wall_tot / 1e3) / 1e9, 3), "unit": "GCUPS",
                 "h2d_bytes_per_step": int(pin_pb.nbytes()),
                 "d2h_bytes_per_step": int(n * 48 + 4 * n + 4 * int(off[-1])),
-                "ms_per_step": round(statistics.mean(wall_ms), 3)},
+                "ms_per_step": round(wall_tot / args.steps, 3)},
         # score path (prep 3, 16-bit kernel, overflow kernel), one traceback
         # launch per wave, the CIGAR gather
         "gpu_launches": args.steps * (5 + info["waves"] + 1),
@@ -365,6 +383,8 @@ def run_traceback(args):
     }
     print(json.dumps(line), flush=True)
     ctx.close()
+    if dist is not None:
+        dist.destroy_process_group()
     return 0
 
 
