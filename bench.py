@@ -153,7 +153,8 @@ def traffic_from_profile(kernel, input_bytes):
 def traffic_tb16(kernel, table_bytes):
     """DRAM bytes of one traceback launch, scaled from the committed capture
     of a smaller case by direction-table bytes (null for another build)."""
-    path = os.path.join(ROOT, "profiles", "tb16_kernel_traffic.json")
+    name = "tbf16_kernel_traffic.json" if kernel.startswith("tbf16") else "tb16_kernel_traffic.json"
+    path = os.path.join(ROOT, "profiles", name)
     if not os.path.exists(path):
         return None
     with open(path) as fh:
@@ -336,19 +337,27 @@ def run_traceback(args):
     t_ms = statistics.mean(tb_ms)
     info = ctx.last_traceback_info()
     packed = info["pairs16"] > 0 and info["pairs32"] * 2 < info["pairs16"]
+    fused = packed and info["fused"] * 2 > info["pairs16"]
     ops_cell = OPS_PER_CELL_TB16 if packed else OPS_PER_CELL_TB
-    achieved = tcells * ops_cell / (t_ms / 1e3) / 1e12
+    # the fused kernel computes the score path's cells (up to termination),
+    # the two-pass kernels the cells up to each end cell
+    units = cells if fused else tcells
+    achieved = units * ops_cell / (t_ms / 1e3) / 1e12
     w = batch.scoring.w
+    minb = dict([(4, 6), (8, 4), (16, 3), (24, 2)])
+    nonempty = (batch.t_len > 0) & (batch.q_len > 0)
     if packed:
         C = next(c for c in (4, 8, 16, 24) if 32 * c - 1 >= w)
-        kernel = f"tb16_kernel<{C}, {dict([(4, 6), (8, 4), (16, 3), (24, 2)])[C]}>"
+        kernel = f"{'tbf16' if fused else 'tb16'}_kernel<{C}, {minb[C]}>"
     else:
         C = next(c for c in (4, 8, 16, 24, 32) if 32 * c - 1 >= w)
         kernel = f"tb_kernel<{C}>"
-    table_bytes = sum(((int(r["mqe_t"]) + int(batch.q_len[i]) - 1) if r["reach_end"] else
-                       (int(r["te"]) + int(r["qe"]))) + 1 for i, r in enumerate(res)
-                      if batch.t_len[i] > 0 and batch.q_len[i] > 0 and
-                      (r["reach_end"] or r["te"] >= 0)) * 32 * C
+    if fused:                 # room for every anti-diagonal of each pair
+        table_bytes = int((batch.t_len[nonempty].astype(np.int64) + batch.q_len[nonempty] - 1).sum()) * 32 * C
+    else:
+        table_bytes = sum(((int(r["mqe_t"]) + int(batch.q_len[i]) - 1) if r["reach_end"] else
+                           (int(r["te"]) + int(r["qe"]))) + 1 for i, r in enumerate(res)
+                          if nonempty[i] and (r["reach_end"] or r["te"] >= 0)) * 32 * C
     line = {
         "metric": "GCUPS with traceback (score path + CIGAR of every extension), bit-exact",
         "value": round(all_cells * args.steps / (k_tot / 1e3) / 1e9, 3), "unit": "GCUPS", "n_gpus": world,
@@ -372,10 +381,12 @@ def run_traceback(args):
         # score path (prep 3, 16-bit kernel, overflow kernel), one traceback
         # launch per wave, the CIGAR gather
         "gpu_launches": args.steps * (5 + info["waves"] + 1),
-        "traceback_pairs": {"lanes16": info["pairs16"], "int32": info["pairs32"], "waves": info["waves"]},
+        "traceback_pairs": {"lanes16": info["pairs16"], "int32": info["pairs32"], "waves": info["waves"],
+                            "fused": info["fused"]},
         "roofline": {"bound": "alu", "achieved": round(achieved, 3), "peak": round(int_peak, 3),
                      "unit": "Tops/s", "frac": round(achieved / int_peak, 4),
                      "traffic": traffic_tb16(kernel, table_bytes) if packed else None,
+                     "units": "score cells" if fused else "cells up to each end cell",
                      "kernel": kernel, "kernel_ms": round(t_ms, 3),
                      "ops_per_cell": ops_cell,
                      "peak_basis": f"{n_sm} SMs x 128 int32 lanes x {sm_max_mhz:.0f} MHz ({peak_kind})"},

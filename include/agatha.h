@@ -69,6 +69,8 @@ extern "C" {
 #define AGATHA_REGS_HIGH   0x80u  /* 16-bit kernel at its larger register
                                      budget (one resident block per SM less)  */
 #define AGATHA_NO_TUNE     0x100u /* ignore the autotuner for this call       */
+#define AGATHA_TB_TWO_PASS 0x200u /* agatha_align_cigar: score path, then a
+                                     separate traceback pass (not fused)    */
 
 /* Flags for agatha_config.flags. */
 #define AGATHA_CFG_TIMING  0x1    /* record CUDA events around the main kernel
@@ -265,11 +267,13 @@ int agatha_align_cigar(agatha_ctx *ctx, const agatha_batch *batch,
  * AGATHA_CFG_TIMING, EAGAIN before the first traceback. */
 int agatha_last_traceback_ms(agatha_ctx *ctx, float *ms);
 
-/* What the last agatha_align_cigar call on ctx ran: pairs given to the
- * 16-bit traceback kernel, pairs the int32 kernel traced (including those
- * the 16-bit kernel handed back), and kernel launches (waves). */
+/* What the last agatha_align_cigar call on ctx ran: pairs given to a 16-bit
+ * traceback kernel, pairs the int32 kernel traced (including those a 16-bit
+ * kernel handed back), kernel launches (waves), and how many of the 16-bit
+ * pairs went through the fused kernel (score path and traceback in one
+ * pass over the band). */
 typedef struct {
-    int64_t pairs16, pairs32, waves, pad;
+    int64_t pairs16, pairs32, waves, fused;
 } agatha_tb_info;
 int agatha_last_traceback_info(agatha_ctx *ctx, agatha_tb_info *info);
 

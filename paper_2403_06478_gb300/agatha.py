@@ -39,6 +39,7 @@ AGATHA_NO_GRAPH = 0x20
 AGATHA_EDGE_PATH_ONLY = 0x40
 AGATHA_REGS_HIGH = 0x80
 AGATHA_NO_TUNE = 0x100
+AGATHA_TB_TWO_PASS = 0x200
 
 AGATHA_CFG_TIMING = 0x1
 AGATHA_CFG_AUTOTUNE = 0x2
@@ -107,7 +108,7 @@ class agatha_serve_stats(ctypes.Structure):
 
 class agatha_tb_info(ctypes.Structure):
     _fields_ = [("pairs16", ctypes.c_int64), ("pairs32", ctypes.c_int64), ("waves", ctypes.c_int64),
-                ("pad", ctypes.c_int64)]
+                ("fused", ctypes.c_int64)]
 
 
 _lib = None
@@ -341,7 +342,8 @@ class Context:
         info = agatha_tb_info()
         _check(lib().agatha_last_traceback_info(self._ptr, ctypes.byref(info)), self._ptr,
                "agatha_last_traceback_info")
-        return {"pairs16": int(info.pairs16), "pairs32": int(info.pairs32), "waves": int(info.waves)}
+        return {"pairs16": int(info.pairs16), "pairs32": int(info.pairs32), "waves": int(info.waves),
+                "fused": int(info.fused)}
 
     def last_traceback_ms(self) -> float:
         ms = ctypes.c_float()

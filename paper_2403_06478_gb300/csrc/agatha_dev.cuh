@@ -235,6 +235,11 @@ cudaError_t launch_tb16_c(const DevBatch *d_batch, const TbItem *items, int32_t 
                           uint8_t *dir, uint32_t *ops, int32_t *n_cigar, int n_blocks, cudaStream_t s);
 template <int C, int MINB>
 int occupancy_tb16_c();
+template <int C, int MINB>
+cudaError_t launch_tbf16_c(const DevBatch *d_batch, const TbItem *items, int32_t n_items, int32_t *head,
+                           uint8_t *dir, uint32_t *ops, int32_t *n_cigar, int n_blocks, cudaStream_t s);
+template <int C, int MINB>
+int occupancy_tbf16_c();
 // Copy each pair's runs (written end first) to dense[dst_off[pair]..] in order.
 cudaError_t launch_cigar_gather(const TbItem *items, int32_t n_items, const int32_t *n_cigar,
                                 const int64_t *dst_off, const uint32_t *ops, uint32_t *dense,

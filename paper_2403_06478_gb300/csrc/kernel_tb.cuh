@@ -229,6 +229,73 @@ tb16_kernel(const DevBatch *__restrict__ d_batch, const TbItem *__restrict__ ite
     }
 }
 
+// Fused score path and traceback on 16-bit lanes: each warp aligns a pair
+// exactly as warp16_align_kernel does (results, termination, hand-back of
+// pairs that leave the 16-bit range to the int32 score kernel's list) while
+// writing the direction bytes of every anti-diagonal it computes, then walks
+// back from the end cell it found.  The table of an item has room for every
+// anti-diagonal of the pair (tlen + qlen - 1 rows) and its run scratch for
+// tlen + qlen runs; a handed-back pair gets n = -1.
+template <int C, int MINB>
+__global__ void __launch_bounds__(WARP_BLOCK_THREADS, MINB)
+tbf16_kernel(const DevBatch *__restrict__ d_batch, const TbItem *__restrict__ items, int32_t n_items,
+             int32_t *head, uint8_t *dir, uint32_t *ops, int32_t *n_cigar) {
+    __shared__ Cold16 cold[WARP_BLOCK_THREADS / 32];
+    __shared__ __align__(16) uint8_t win[WARP_BLOCK_THREADS / 32][TB_WIN_ROWS * TbLayout<C, true>::WB];
+    const DevBatch B = *d_batch;
+    const int lane = threadIdx.x & 31;
+    uint8_t *my_win = win[threadIdx.x >> 5];
+    for (;;) {
+        int32_t k = 0;
+        if (lane == 0) k = atomicAdd(head, 1);
+        k = __shfl_sync(FULL, k, 0);
+        if (k >= n_items) break;
+        const TbItem it = items[k];
+        uint8_t *dt = dir + it.dir_off;
+        bool ok;
+        int32_t et, eq;
+        {
+            WarpPair16<C, (MINB < 4 && C <= 16) || MINB < 3, true, true, true> wp(cold[threadIdx.x >> 5]);
+            ok = wp.run(B, it.pair, lane, true, dt);
+            et = wp.end_t;
+            eq = wp.end_q;
+        }
+        if (!ok) {                                  // the int32 score kernel takes it
+            if (lane == 0) {
+                const int32_t slot = atomicAdd(&B.counters[CTR_NOVF], 1);
+                B.ovf_list[slot] = it.pair;
+                n_cigar[it.pair] = -1;
+            }
+            continue;
+        }
+        if (et < 0 || eq < 0) {                     // the maximum is the origin
+            if (lane == 0) n_cigar[it.pair] = 0;
+            continue;
+        }
+        __syncwarp();
+        const int32_t w = effective_w(B.params.w, B.t_len[it.pair], B.q_len[it.pair]);
+        const int32_t n = tb_walk<C, true>(my_win, dt, ops + it.ops_off, et + eq + 2, et, eq, w, lane);
+        if (lane == 0) n_cigar[it.pair] = n;
+    }
+}
+
+template <int C, int MINB>
+cudaError_t launch_tbf16_c(const DevBatch *d_batch, const TbItem *items, int32_t n_items, int32_t *head,
+                           uint8_t *dir, uint32_t *ops, int32_t *n_cigar, int n_blocks, cudaStream_t s) {
+    tbf16_kernel<C, MINB><<<n_blocks, WARP_BLOCK_THREADS, 0, s>>>(d_batch, items, n_items, head, dir, ops,
+                                                                  n_cigar);
+    return cudaGetLastError();
+}
+
+template <int C, int MINB>
+int occupancy_tbf16_c() {
+    int nb = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, tbf16_kernel<C, MINB>, WARP_BLOCK_THREADS, 0) !=
+        cudaSuccess)
+        return 1;
+    return nb > 0 ? nb : 1;
+}
+
 template <int C>
 cudaError_t launch_tb_c(const DevBatch *d_batch, const TbItem *items, int32_t n_items, int32_t *head,
                         uint8_t *dir, uint32_t *ops, int32_t *n_cigar, int n_blocks, cudaStream_t s) {

@@ -103,7 +103,12 @@ struct Cold16 {
 //   bits 4-7  Eo, Fo, E2o, F2o leaving the cell extend the cell's own gap
 //             state (strictly better than opening from H)
 // Each bit is one 16x2 minimum of an exclusive or (0 or 1 per half).
-template <int C, bool DMREG, bool DEFER = false, bool DIR = false>
+// SCORE: the termination test and the result (the score path).  DIR with
+// SCORE is the fused traceback variant: the score path itself writes the
+// direction bytes of every anti-diagonal it computes, so the traceback needs
+// no second pass over the band; without SCORE (run_dir) the end anti-diagonal
+// is given and nothing else is tracked.
+template <int C, bool DMREG, bool DEFER = false, bool DIR = false, bool SCORE = !DIR>
 struct WarpPair16 {
     static_assert(C == 4 || C == 8 || C == 16 || C == 24, "16-bit lanes use 4, 8, 16 or 24 slots per lane");
     static constexpr int P = C / 2;
@@ -133,6 +138,7 @@ struct WarpPair16 {
     uint32_t DMR[DMREG ? P : 1];   // DMREG: dead_mask(p), computed once per pair
     uint32_t Hsave[DEFER ? P : 1]; // DEFER: H of the pending maximum's anti-diagonal
     uint8_t *dtab;                 // DIR: this lane's bytes of anti-diagonal 0
+    int32_t end_t, end_q;          // DIR and SCORE: where the traceback starts (-1: empty)
     int32_t pend_r, pend_m, pend_lm;   // its anti-diagonal (-3: none), maximum, lane maximum
     // base windows (2 bits per slot): Tw field jl = T[B + j0 + jl],
     // Qw field jl = Q[r - B - j0 - jl]
@@ -505,7 +511,10 @@ struct WarpPair16 {
             else if (i == P - 1) lmax = __vmaxu2(lmax, mx);
             else pend = mx;
         }
-        if constexpr (DIR) return dir_finish<ODD, MODE>(r, lmax, rb, vb, dbits);
+        if constexpr (DIR && !SCORE) return dir_finish<ODD, MODE>(r, lmax, rb, vb, dbits);
+        if constexpr (DIR && SCORE) {
+            if (r >= 0) store_row(r, dbits);
+        }
         if constexpr (MODE == BULK) {
             // (the band cells of bulk anti-diagonals are counted by run())
             // slots beyond the band sit above every band slot of their lane, so
@@ -551,27 +560,31 @@ struct WarpPair16 {
                (__vminu2(E2o[p] ^ hoe2, one) << 6) + (__vminu2(F2o[p] ^ hoe2, one) << 7);
     }
 
-    // DIR: end of a step.  Store the row, then what the rebase needs: the
-    // anti-diagonal maximum (only when a rebase follows) and the rebase.
+    // DIR: the lane's C bytes of anti-diagonal r, one vector store
+    __device__ __forceinline__ void store_row(int32_t r, const uint32_t (&db)[P]) const {
+        uint32_t wd[C / 4];
+#pragma unroll
+        for (int k = 0; k < C / 4; ++k) wd[k] = prmt(db[2 * k], db[2 * k + 1], 0x6420);
+        uint8_t *p = dtab + (int64_t)r * (32 * C);
+        if constexpr (C % 16 == 0) {
+#pragma unroll
+            for (int k = 0; k < C / 16; ++k)
+                reinterpret_cast<uint4 *>(p)[k] = make_uint4(wd[4 * k], wd[4 * k + 1], wd[4 * k + 2], wd[4 * k + 3]);
+        } else if constexpr (C % 8 == 0) {
+#pragma unroll
+            for (int k = 0; k < C / 8; ++k) reinterpret_cast<uint2 *>(p)[k] = make_uint2(wd[2 * k], wd[2 * k + 1]);
+        } else {
+            *reinterpret_cast<uint32_t *>(p) = wd[0];
+        }
+    }
+
+    // DIR without SCORE: end of a step.  Store the row, then what the rebase
+    // needs: the anti-diagonal maximum (only when a rebase follows) and the
+    // rebase.
     template <bool ODD, int MODE>
     __device__ __forceinline__ bool dir_finish(int32_t r, uint32_t lmax, uint32_t rb, uint32_t vb,
                                                const uint32_t (&db)[P]) {
-        if (r >= 0) {
-            uint32_t wd[C / 4];
-#pragma unroll
-            for (int k = 0; k < C / 4; ++k) wd[k] = prmt(db[2 * k], db[2 * k + 1], 0x6420);
-            uint8_t *p = dtab + (int64_t)r * (32 * C);
-            if constexpr (C % 16 == 0) {
-#pragma unroll
-                for (int k = 0; k < C / 16; ++k)
-                    reinterpret_cast<uint4 *>(p)[k] = make_uint4(wd[4 * k], wd[4 * k + 1], wd[4 * k + 2], wd[4 * k + 3]);
-            } else if constexpr (C % 8 == 0) {
-#pragma unroll
-                for (int k = 0; k < C / 8; ++k) reinterpret_cast<uint2 *>(p)[k] = make_uint2(wd[2 * k], wd[2 * k + 1]);
-            } else {
-                *reinterpret_cast<uint32_t *>(p) = wd[0];
-            }
-        }
+        if (r >= 0) store_row(r, db);
         if constexpr (MODE == BULK) {
             // fast_pair rebases after the odd step of a pair
             if (ODD && until_rebase <= 4) {
@@ -681,7 +694,10 @@ struct WarpPair16 {
 
     // ------------------------------------------------------------------ pair
     // Returns false if the pair must be recomputed with int32 lanes.
-    __device__ __forceinline__ bool run(const DevBatch &Bt, int32_t pair, int32_t lane_, bool use_fast) {
+    // DIR (fused): dt is the pair's direction table, one row per anti-diagonal
+    // up to the last one the extension can reach.
+    __device__ __forceinline__ bool run(const DevBatch &Bt, int32_t pair, int32_t lane_, bool use_fast,
+                                        uint8_t *dt = nullptr) {
         prm = Bt.params;
         lane = lane_;
         tlen = Bt.t_len[pair]; qlen = Bt.q_len[pair];
@@ -698,6 +714,7 @@ struct WarpPair16 {
             qspan = (int32_t)min(Bt.q_words - qw0, (int64_t)((qph + qlen + 15) >> 4));
         }
         agatha_result *out = Bt.out + pair;
+        if constexpr (DIR) { end_t = -1; end_q = -1; }
         if (tlen <= 0 || qlen <= 0) {
             if (lane == 0) write_empty_result(out);
             return true;
@@ -706,6 +723,7 @@ struct WarpPair16 {
         oe = prm.q + prm.e; oe2 = prm.q2 + prm.e2;
         j0 = lane * C;
         last_r = tlen + qlen - 2;
+        if constexpr (DIR) dtab = dt + j0;
         {
             const int32_t Dp = step_change_max(prm), kint = rebase_interval(Dp);
             until_rebase = kint;
@@ -791,6 +809,12 @@ struct WarpPair16 {
             stop = tail_step(r);
         }
         if (ovf) return false;
+        if constexpr (DIR) {
+            // the traceback's start: the query end when reached, else the maximum
+            const bool reach = !zdropped && cold.mqe != K_NEG_OUT && cold.mqe + prm.end_bonus > gmax;
+            end_t = reach ? cold.mqe_t : cold.gt;
+            end_q = reach ? qlen - 1 : cold.gq;
+        }
         if (lane == 0) {
             agatha_result o;
             const int32_t mqe = cold.mqe;

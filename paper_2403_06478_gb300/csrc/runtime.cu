@@ -179,6 +179,10 @@ static cudaError_t launch_warp16(int C, int high, const DevBatch *d, int blocks,
     }
 }
 
+cudaError_t launch_overflow_int32(const Slot *sl, const LaunchPlan &lp, cudaStream_t s) {
+    return launch_warp(lp.C, sl->d_desc, lp.warp_blocks, s, lp.fast, WARP_LIST_OVERFLOW);
+}
+
 int warp16_occupancy(int C, int high) {
     switch (C * 2 + high) {
         case 8: return occupancy_warp16_c<4, 6>();
@@ -524,9 +528,10 @@ extern "C" const char *agatha_last_error(agatha_ctx *ctx) {
 
 namespace agatha {
 
-// Stage one batch on the context's slot and run it with plan lp (ctx->mu held).
-int run_planned(agatha_ctx *ctx, const agatha_batch *batch, const DevParams &p, agatha_result *out,
-                uint32_t flags, cudaStream_t s, const LaunchPlan &lp, cudaEvent_t ev0, cudaEvent_t ev1) {
+// Copy one batch (host arrays) or point at it (device arrays) and write the
+// descriptor of the context's slot for plan lp (ctx->mu held).
+int stage_batch(agatha_ctx *ctx, const agatha_batch *batch, const DevParams &p, agatha_result *out,
+                uint32_t flags, cudaStream_t s, const LaunchPlan &lp) {
     const bool dev = (flags & AGATHA_DEVICE_PTRS) != 0;
     const int64_t n = batch->n_pairs;
     cudaError_t e;
@@ -573,6 +578,18 @@ int run_planned(agatha_ctx *ctx, const agatha_batch *batch, const DevParams &p, 
     if ((e = cudaMemcpyAsync(sl->d_desc, d, sizeof(DevBatch), cudaMemcpyHostToDevice, s)) != cudaSuccess)
         return cuda_fail(ctx, e, "copy descriptor");
     sl->last_stream = s;
+    return AGATHA_OK;
+}
+
+// Stage one batch on the context's slot and run it with plan lp (ctx->mu held).
+int run_planned(agatha_ctx *ctx, const agatha_batch *batch, const DevParams &p, agatha_result *out,
+                uint32_t flags, cudaStream_t s, const LaunchPlan &lp, cudaEvent_t ev0, cudaEvent_t ev1) {
+    const bool dev = (flags & AGATHA_DEVICE_PTRS) != 0;
+    const int64_t n = batch->n_pairs;
+    cudaError_t e;
+    int rc;
+    Slot *sl = &ctx->main;
+    if ((rc = stage_batch(ctx, batch, p, out, flags, s, lp))) return rc;
     if ((e = slot_run(ctx, sl, lp, s, ev0, ev1)) != cudaSuccess) return cuda_fail(ctx, e, "launch");
     if ((e = cudaMemcpyAsync(sl->h_counters, sl->counters.ptr, CTR_COUNT * sizeof(int32_t),
                              cudaMemcpyDeviceToHost, s)) != cudaSuccess)

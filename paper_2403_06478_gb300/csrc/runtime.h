@@ -125,6 +125,12 @@ cudaError_t slot_run(agatha_ctx *ctx, Slot *s, const LaunchPlan &lp, cudaStream_
 // Stop and free the context's server, if any (serve.cu).
 void serve_free(agatha_ctx *ctx);
 
+// Copy (host arrays) or reference (device arrays) one batch on the context's
+// own slot and write its descriptor for plan lp, without launching anything.
+int stage_batch(agatha_ctx *ctx, const agatha_batch *batch, const DevParams &p, agatha_result *out,
+                uint32_t flags, cudaStream_t s, const LaunchPlan &lp);
+// The int32 kernel over the 16-bit kernels' hand-back list of the slot's batch.
+cudaError_t launch_overflow_int32(const Slot *sl, const LaunchPlan &lp, cudaStream_t s);
 // Stage one batch on the context's own slot and run it with plan lp; ev0/ev1
 // (may be null) bracket the alignment kernels.  ctx->mu must be held.
 int run_planned(agatha_ctx *ctx, const agatha_batch *batch, const DevParams &p, agatha_result *out,

@@ -81,6 +81,26 @@ cudaError_t launch_tb16(int C, const DevBatch *d, const TbItem *items, int32_t n
     }
 }
 
+// fused score path and traceback on 16-bit lanes
+cudaError_t launch_tbf16(int C, const DevBatch *d, const TbItem *items, int32_t n, int32_t *head,
+                         uint8_t *dir, uint32_t *ops, int32_t *ncig, int blocks, cudaStream_t s) {
+    switch (C) {
+        case 4: return launch_tbf16_c<4, 6>(d, items, n, head, dir, ops, ncig, blocks, s);
+        case 8: return launch_tbf16_c<8, 4>(d, items, n, head, dir, ops, ncig, blocks, s);
+        case 16: return launch_tbf16_c<16, 3>(d, items, n, head, dir, ops, ncig, blocks, s);
+        default: return launch_tbf16_c<24, 2>(d, items, n, head, dir, ops, ncig, blocks, s);
+    }
+}
+
+int tbf16_occupancy(int C) {
+    switch (C) {
+        case 4: return occupancy_tbf16_c<4, 6>();
+        case 8: return occupancy_tbf16_c<8, 4>();
+        case 16: return occupancy_tbf16_c<16, 3>();
+        default: return occupancy_tbf16_c<24, 2>();
+    }
+}
+
 int tb16_occupancy(int C) {
     switch (C) {
         case 4: return occupancy_tb16_c<4, 6>();
@@ -154,28 +174,44 @@ extern "C" int agatha_align_cigar(agatha_ctx *ctx, const agatha_batch *batch, co
         return set_error(ctx, AGATHA_ENOTSUP, "traceback takes bands up to 1023 cells (this batch: %d)",
                          shape.max_w_all);
 
-    // 1. score path
+    // 1. plan: the fused kernel (score path and traceback in one pass, on
+    //    16-bit lanes) unless the scoring or the flags rule 16-bit lanes out
+    //    or ask for the two-pass form
     LaunchPlan lp;
     if ((rc = make_plan(ctx, p, shape, flags, &lp))) return rc;
-    if ((rc = tune_apply(ctx, batch, p, flags, s, &lp))) return rc;
-    if ((rc = run_planned(ctx, batch, p, out, flags, s, lp, ctx->timing ? ctx->ev_k0 : nullptr,
-                          ctx->timing ? ctx->ev_k1 : nullptr)))
-        return rc;
-    ctx->timed_once = true;
-
-    // 2. items, longest predicted work first
     const int C32 = pick_slots_per_lane(std::max<int32_t>(shape.max_w_all, 1));
     const int C16 = pick_slots16(std::max<int32_t>(shape.max_w_all, 1));
     const bool use16 = C16 > 0 && step_change_max(p) <= STEP16_MAX && !(flags & AGATHA_FORCE32);
+    const bool fused = use16 && lp.lane16 && !lp.wide_w && !(flags & (AGATHA_PLAIN | AGATHA_TB_TWO_PASS));
+    Slot *sl = &ctx->main;
+    if (fused) {
+        if ((rc = stage_batch(ctx, batch, p, out, flags, s, lp))) return rc;
+        if ((e = cudaMemsetAsync(sl->counters.ptr, 0, CTR_COUNT * sizeof(int32_t), s)))
+            return cuda_fail(ctx, e, "clear counters");
+    } else {
+        // the score path first: its results give each pair's end cell
+        if ((rc = tune_apply(ctx, batch, p, flags, s, &lp))) return rc;
+        if ((rc = run_planned(ctx, batch, p, out, flags, s, lp, ctx->timing ? ctx->ev_k0 : nullptr,
+                              ctx->timing ? ctx->ev_k1 : nullptr)))
+            return rc;
+        ctx->timed_once = true;
+    }
+
+    // 2. items, longest predicted work first.  A fused item covers every
+    //    anti-diagonal of its pair (its end is found on the way); a two-pass
+    //    item ends at its end cell.
     std::vector<TbItem> items;
     items.reserve((size_t)n);
     for (int64_t i = 0; i < n; ++i) {
         const int32_t tl = batch->t_len[i], ql = batch->q_len[i];
         if (tl <= 0 || ql <= 0) continue;
-        const agatha_result &r = out[i];
-        const int32_t et = r.reach_end ? r.mqe_t : r.te;
-        const int32_t eq = r.reach_end ? ql - 1 : r.qe;
-        if (et < 0 || eq < 0) continue;                 // the maximum is the origin: empty CIGAR
+        int32_t et = tl - 1, eq = ql - 1;
+        if (!fused) {
+            const agatha_result &r = out[i];
+            et = r.reach_end ? r.mqe_t : r.te;
+            eq = r.reach_end ? ql - 1 : r.qe;
+            if (et < 0 || eq < 0) continue;             // the maximum is the origin: empty CIGAR
+        }
         TbItem it;
         it.pair = (int32_t)i; it.end_t = et; it.end_q = eq; it.pad = 0;
         it.dir_off = 0; it.ops_off = 0;
@@ -202,10 +238,13 @@ extern "C" int agatha_align_cigar(agatha_ctx *ctx, const agatha_batch *batch, co
         ops_total += (int64_t)it.end_t + it.end_q + 2;
     }
 
-    // 3. buffers, then waves of the 16-bit kernel and of the int32 kernel
+    // 3. buffers, then waves of each kernel
     TbBufs &tb = ctx->tb;
+    // (the dense copy of the runs is sized here too, to its bound, so that the
+    // direction tables may take whatever is left)
     if ((rc = ensure_exact(ctx, tb.items, (size_t)std::max<int64_t>(2 * n_items, 1) * sizeof(TbItem))) ||
         (rc = ensure_exact(ctx, tb.ops, (size_t)std::max<int64_t>(ops_total, 1) * 4)) ||
+        (rc = ensure_exact(ctx, tb.dense, (size_t)std::max<int64_t>(ops_total, 1) * 4)) ||
         (rc = ensure_exact(ctx, tb.n_cigar, (size_t)n * 4)) ||
         (rc = ensure_exact(ctx, tb.heads, (size_t)std::max<int64_t>(2 * n_items, 1) * 4)) ||
         (rc = ensure_exact(ctx, tb.dst_off, (size_t)(n + 1) * 8)))
@@ -220,10 +259,11 @@ extern "C" int agatha_align_cigar(agatha_ctx *ctx, const agatha_batch *batch, co
     }
     ctx->tb_ms = 0.f;
     int64_t item_base = 0, head_base = 0;     // where this kind's items / queue heads start
+    enum { K_INT32 = 0, K_16 = 1, K_FUSED = 2 };
     // one kind of kernel over `list`: waves whose tables fit, each one launch
-    auto run_kind = [&](std::vector<TbItem> &list, bool packed) -> int {
+    auto run_kind = [&](std::vector<TbItem> &list, int kind) -> int {
         if (list.empty()) return AGATHA_OK;
-        const int C = packed ? C16 : C32;
+        const int C = kind == K_INT32 ? C32 : C16;
         const int64_t row = 32 * C;
         int64_t total = 0, largest = 0;
         for (const TbItem &it : list) {
@@ -255,15 +295,18 @@ extern "C" int agatha_align_cigar(agatha_ctx *ctx, const agatha_batch *batch, co
                                          cudaMemcpyHostToDevice, s);
         if (e2 != cudaSuccess) return cuda_fail(ctx, e2, "copy traceback items");
         if (ctx->timing && (e2 = cudaEventRecord(ctx->ev_tb0, s)) != cudaSuccess) return cuda_fail(ctx, e2, "event");
-        const int resident = ctx->n_sm * (packed ? tb16_occupancy(C) : tb_occupancy(C));
+        const int occ = kind == K_INT32 ? tb_occupancy(C) : (kind == K_16 ? tb16_occupancy(C) : tbf16_occupancy(C));
+        const int resident = ctx->n_sm * occ;
         for (size_t wv = 0; wv + 1 < begin.size(); ++wv) {
             const int64_t b = begin[wv], cnt = begin[wv + 1] - b;
             const int blocks = (int)std::max<int64_t>(1, std::min<int64_t>(resident, (cnt + 3) / 4));
             int32_t *head = (int32_t *)tb.heads.ptr + head_base + (int64_t)wv;
-            e2 = packed ? launch_tb16(C, ctx->main.d_desc, d_items + b, (int32_t)cnt, head, (uint8_t *)tb.dir.ptr,
-                                      (uint32_t *)tb.ops.ptr, (int32_t *)tb.n_cigar.ptr, blocks, s)
-                        : launch_tb(C, ctx->main.d_desc, d_items + b, (int32_t)cnt, head, (uint8_t *)tb.dir.ptr,
-                                    (uint32_t *)tb.ops.ptr, (int32_t *)tb.n_cigar.ptr, blocks, s);
+            uint8_t *dir = (uint8_t *)tb.dir.ptr;
+            uint32_t *ops = (uint32_t *)tb.ops.ptr;
+            int32_t *ncg = (int32_t *)tb.n_cigar.ptr;
+            if (kind == K_FUSED) e2 = launch_tbf16(C, sl->d_desc, d_items + b, (int32_t)cnt, head, dir, ops, ncg, blocks, s);
+            else if (kind == K_16) e2 = launch_tb16(C, sl->d_desc, d_items + b, (int32_t)cnt, head, dir, ops, ncg, blocks, s);
+            else e2 = launch_tb(C, sl->d_desc, d_items + b, (int32_t)cnt, head, dir, ops, ncg, blocks, s);
             if (e2 != cudaSuccess) return cuda_fail(ctx, e2, "traceback launch");
         }
         if (ctx->timing && (e2 = cudaEventRecord(ctx->ev_tb1, s)) != cudaSuccess) return cuda_fail(ctx, e2, "event");
@@ -276,23 +319,72 @@ extern "C" int agatha_align_cigar(agatha_ctx *ctx, const agatha_batch *batch, co
         }
         item_base += (int64_t)list.size();
         head_base += (int64_t)begin.size() - 1;
-        (packed ? ctx->tb_info.pairs16 : ctx->tb_info.pairs32) += (int64_t)list.size();
+        (kind == K_INT32 ? ctx->tb_info.pairs32 : ctx->tb_info.pairs16) += (int64_t)list.size();
+        if (kind == K_FUSED) ctx->tb_info.fused += (int64_t)list.size();
         ctx->tb_info.waves += (int64_t)begin.size() - 1;
         return AGATHA_OK;
     };
     ctx->tb_info = agatha_tb_info{0, 0, 0, 0};
     std::vector<int32_t> ncig((size_t)n);
     std::vector<TbItem> rest;
-    if (use16) {
-        if ((rc = run_kind(items, true))) return rc;
+    if (fused) {
+        if ((rc = run_kind(items, K_FUSED))) return rc;
+        // pairs handed back (scores left the 16-bit range): the int32 score
+        // kernel over the hand-back list, bracketed as the score kernels
+        if (ctx->timing && (e = cudaEventRecord(ctx->ev_k0, s))) return cuda_fail(ctx, e, "event");
+        if ((e = launch_overflow_int32(sl, lp, s))) return cuda_fail(ctx, e, "launch");
+        if (ctx->timing && (e = cudaEventRecord(ctx->ev_k1, s))) return cuda_fail(ctx, e, "event");
+        ctx->timed_once = true;
+        if ((e = cudaMemcpyAsync(out, sl->out.ptr, (size_t)n * sizeof(agatha_result), cudaMemcpyDeviceToHost, s)) ||
+            (e = cudaMemcpyAsync(ncig.data(), tb.n_cigar.ptr, (size_t)n * 4, cudaMemcpyDeviceToHost, s)) ||
+            (e = cudaStreamSynchronize(s)))
+            return cuda_fail(ctx, e, "copy results");
+        // pairs with an empty sequence are no items: their result is the
+        // empty one the score kernels write
+        for (int64_t i = 0; i < n; ++i) {
+            if (batch->t_len[i] > 0 && batch->q_len[i] > 0) continue;
+            agatha_result &o = out[i];
+            o.max = 0; o.qe = -1; o.te = -1;
+            o.gscore = AGATHA_NEG_INF; o.mqe = AGATHA_NEG_INF; o.mte = AGATHA_NEG_INF;
+            o.mqe_t = -1; o.mte_q = -1;
+            o.cells = 0;
+            o.zdropped = 0; o.reach_end = 0; o.lane16 = 0;
+            for (int k = 0; k < 5; ++k) o.pad[k] = 0;
+        }
+        for (const TbItem &it0 : items) {
+            if (ncig[it0.pair] >= 0) continue;
+            const agatha_result &r = out[it0.pair];
+            TbItem it = it0;
+            it.end_t = r.reach_end ? r.mqe_t : r.te;
+            it.end_q = r.reach_end ? batch->q_len[it.pair] - 1 : r.qe;
+            if (it.end_t < 0 || it.end_q < 0) continue;   // stays n = -1: fixed below
+            rest.push_back(it);
+        }
+        // an empty path of a handed-back pair
+        for (const TbItem &it0 : items)
+            if (ncig[it0.pair] < 0) {
+                const agatha_result &r = out[it0.pair];
+                const int32_t et = r.reach_end ? r.mqe_t : r.te;
+                const int32_t eq = r.reach_end ? batch->q_len[it0.pair] - 1 : r.qe;
+                if (et < 0 || eq < 0) {
+                    const int32_t zero = 0;
+                    if ((e = cudaMemcpyAsync((int32_t *)tb.n_cigar.ptr + it0.pair, &zero, 4,
+                                             cudaMemcpyHostToDevice, s)) || (e = cudaStreamSynchronize(s)))
+                        return cuda_fail(ctx, e, "run count");
+                }
+            }
+        if ((rc = run_kind(rest, K_INT32))) return rc;
+    } else if (use16) {
+        if ((rc = run_kind(items, K_16))) return rc;
         if ((e = cudaMemcpy(ncig.data(), tb.n_cigar.ptr, (size_t)n * 4, cudaMemcpyDeviceToHost)))
             return cuda_fail(ctx, e, "traceback run counts");
         for (const TbItem &it : items)
             if (ncig[it.pair] < 0) rest.push_back(it);      // scores left the 16-bit range
+        if ((rc = run_kind(rest, K_INT32))) return rc;
     } else {
         rest = items;
+        if ((rc = run_kind(rest, K_INT32))) return rc;
     }
-    if ((rc = run_kind(rest, false))) return rc;
 
     // 4. layout in input order, gather, copy back
     if ((e = cudaMemcpyAsync(ncig.data(), tb.n_cigar.ptr, (size_t)n * 4, cudaMemcpyDeviceToHost, s)) ||

@@ -14,7 +14,8 @@ from paper_2403_06478_gb300 import build as B  # noqa: E402
 from paper_2403_06478_gb300 import workload as W  # noqa: E402
 
 FLAGS = {"batched": 0, "plain": A.AGATHA_PLAIN, "force32": A.AGATHA_FORCE32,
-         "edge": A.AGATHA_EDGE_PATH_ONLY, "regs_high": A.AGATHA_REGS_HIGH}
+         "edge": A.AGATHA_EDGE_PATH_ONLY, "regs_high": A.AGATHA_REGS_HIGH,
+         "two_pass": A.AGATHA_TB_TWO_PASS}
 
 
 def main():

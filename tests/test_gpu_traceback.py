@@ -78,24 +78,32 @@ def _check(ctx, batch, label, idx=None, flags=0):
     return res, off, cig
 
 
-def _kernels(ctx, res, batch, packed):
-    """The traceback kernel that ran: every traced pair on 16-bit lanes (none
-    handed back) or every one on int32 lanes."""
+# the three traceback forms: fused (default), two-pass on 16-bit lanes, int32
+TB_FLAGS = [0, A.AGATHA_TB_TWO_PASS, A.AGATHA_FORCE32]
+
+
+def _kernels(ctx, res, batch, flags):
+    """The traceback kernel that ran, and that no pair was handed back: the
+    fused kernel takes every non-empty pair, the two-pass kernels every pair
+    with a path (16-bit lanes unless FORCE32)."""
     info = ctx.last_traceback_info()
     et, _ = _end_cells(res, batch)
     traced = int((et >= 0).sum())
-    if packed:
-        assert info["pairs16"] == traced and info["pairs32"] == 0, info
+    nonempty = int(((batch.t_len > 0) & (batch.q_len > 0)).sum())
+    if flags & A.AGATHA_FORCE32:
+        assert info["pairs16"] == 0 and info["pairs32"] == traced and info["fused"] == 0, info
+    elif flags & (A.AGATHA_TB_TWO_PASS | A.AGATHA_PLAIN):
+        assert info["pairs16"] == traced and info["pairs32"] == 0 and info["fused"] == 0, info
     else:
-        assert info["pairs16"] == 0 and info["pairs32"] == traced, info
+        assert info["pairs16"] == nonempty == info["fused"] and info["pairs32"] == 0, info
     assert info["waves"] >= (1 if traced else 0)
 
 
-@pytest.mark.parametrize("flags", [0, A.AGATHA_PLAIN, A.AGATHA_FORCE32])
+@pytest.mark.parametrize("flags", TB_FLAGS + [A.AGATHA_PLAIN])
 def test_small_config_every_pair(ctx, flags):
     batch = W.make_config("small")
     res, _, _ = _check(ctx, batch, f"small/{flags}", flags=flags)
-    _kernels(ctx, res, batch, packed=not flags & A.AGATHA_FORCE32)
+    _kernels(ctx, res, batch, flags)
     assert ctx.last_traceback_ms() > 0
 
 
@@ -103,16 +111,16 @@ def test_small_config_every_pair(ctx, flags):
 def test_adversarial_pairs(ctx, si):
     scoring = ADVERSARIAL_SCORINGS[si]
     batch = _adversarial_batch(np.random.default_rng(100 + si), scoring)
-    for flags in (0, A.AGATHA_FORCE32):
+    for flags in TB_FLAGS:
         _check(ctx, batch, f"adversarial[{si}]/{flags}", flags=flags)
 
 
 @pytest.mark.parametrize("name,n", [("ont", 120), ("hifi", 120), ("skewed", 600)])
-@pytest.mark.parametrize("flags", [0, A.AGATHA_FORCE32])
+@pytest.mark.parametrize("flags", TB_FLAGS)
 def test_workload_mixes_every_pair(ctx, name, n, flags):
     batch = W.make_config(name, n_pairs=n)
     res, _, _ = _check(ctx, batch, f"{name}/{flags}", flags=flags)
-    _kernels(ctx, res, batch, packed=not flags)
+    _kernels(ctx, res, batch, flags)
 
 
 def test_16bit_overflow_hands_pairs_to_int32(ctx):
@@ -133,10 +141,12 @@ def test_16bit_overflow_hands_pairs_to_int32(ctx):
         qs.append(x)
         ts.append(x.copy())
     batch = W.from_pairs(qs, ts, scoring)
-    res, _, _ = _check(ctx, batch, "overflow")
-    assert (res["lane16"][:4] == 0).all()           # the score path recomputed them too
-    info = ctx.last_traceback_info()
-    assert info["pairs16"] == 9 and 1 <= info["pairs32"] <= 4, info
+    for flags in (0, A.AGATHA_TB_TWO_PASS):
+        res, _, _ = _check(ctx, batch, f"overflow/{flags}", flags=flags)
+        assert (res["lane16"][:4] == 0).all()       # recomputed on int32 lanes
+        assert (res["lane16"][4:] == 1).all()
+        info = ctx.last_traceback_info()
+        assert info["pairs16"] == 9 and 1 <= info["pairs32"] <= 4, info
 
 
 @pytest.mark.parametrize("scoring", [
@@ -157,7 +167,7 @@ def test_steep_and_tied_scorings(ctx, scoring):
             qs.append(x)
             ts.append(y[: L - cut] if k % 2 else np.concatenate([y, rng.integers(0, 4, cut)]).astype(np.uint8))
     batch = W.from_pairs(qs, ts, scoring)
-    for flags in (0, A.AGATHA_FORCE32):
+    for flags in TB_FLAGS:
         _check(ctx, batch, f"steep/{scoring}/{flags}", flags=flags)
 
 
@@ -192,14 +202,17 @@ def test_errors(ctx):
     _check(ctx, W.make_config("small", n_pairs=32), "after errors")
 
 
-def test_waves_under_a_small_budget():
+@pytest.mark.parametrize("flags", [0, A.AGATHA_TB_TWO_PASS])
+def test_waves_under_a_small_budget(flags):
     # a budget that holds the tables of only a few pairs at a time: many
     # waves, same CIGARs as one wave
     batch = W.make_config("ont", n_pairs=60)
     with A.Context(0) as big:
-        r1, o1, c1 = big.align_cigar(A.pack_batch(batch), batch.scoring)
-    with A.Context(0, mem_budget_bytes=400 << 20) as small:
-        r2, o2, c2 = small.align_cigar(A.pack_batch(batch), batch.scoring)
+        r1, o1, c1 = big.align_cigar(A.pack_batch(batch), batch.scoring, flags=flags)
+        assert big.last_traceback_info()["waves"] == 1
+    with A.Context(0, mem_budget_bytes=120 << 20) as small:
+        r2, o2, c2 = small.align_cigar(A.pack_batch(batch), batch.scoring, flags=flags)
+        assert small.last_traceback_info()["waves"] > 1
     assert A.results_equal(r1, r2).size == 0
     assert np.array_equal(o1, o2) and np.array_equal(c1, c2)
 
@@ -211,4 +224,4 @@ def test_ont_full_size_sampled(ctx):
     longest = np.argsort(-(batch.q_len.astype(np.int64) + batch.t_len))[:6]
     idx = np.unique(np.concatenate([longest, rng.choice(batch.n_pairs, 40, replace=False)]))
     res, _, _ = _check(ctx, batch, "ont/full", idx=idx)
-    _kernels(ctx, res, batch, packed=True)
+    _kernels(ctx, res, batch, 0)
