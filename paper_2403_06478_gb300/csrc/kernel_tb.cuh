@@ -255,7 +255,10 @@ tbf16_kernel(const DevBatch *__restrict__ d_batch, const TbItem *__restrict__ it
         bool ok;
         int32_t et, eq;
         {
-            WarpPair16<C, (MINB < 4 && C <= 16) || MINB < 3, true, true, true> wp(cold[threadIdx.x >> 5]);
+            // without the deferred arg-max (DEFER): its saved registers cost
+            // more here, beside the direction bits, than the searches they save
+            // (measured on the ONT-like batch: 171 against 179 ms)
+            WarpPair16<C, (MINB < 4 && C <= 16) || MINB < 3, false, true, true> wp(cold[threadIdx.x >> 5]);
             ok = wp.run(B, it.pair, lane, true, dt);
             et = wp.end_t;
             eq = wp.end_q;
