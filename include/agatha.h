@@ -241,18 +241,22 @@ int agatha_tune_variants(agatha_ctx *ctx, const agatha_params *params, int32_t w
  *   cigar:     host array of cigar_cap runs.  The runs of pair i number at
  *              most t_len[i] + q_len[i]; on ERANGE (cigar_off[n] > cap)
  *              nothing is written to it.
- * Kernels: the traceback recomputes each band up to its end cell and
- * records one direction byte per slot, on 16-bit packed lanes when the
- * scoring allows them (as for the score path; AGATHA_FORCE32 turns them off)
- * and on int32 lanes otherwise or for a pair whose scores leave the 16-bit
- * range; both give the same CIGARs.
- * Device memory: besides the score path's buffers, a direction table of one
- * byte per band slot and anti-diagonal up to each end cell (32*C bytes per
- * anti-diagonal, C the kernel's slots per lane for the batch's widest band:
- * 4, 8, 16 or 24 on 16-bit lanes, up to 32 on int32 lanes).  Pairs run in
- * waves whose tables fit in the context's budget (else in the device's free
- * memory less min(1/16 of it, 4 GiB)); the context keeps the largest table
- * made until agatha_destroy.
+ * Kernels: when the scoring allows 16-bit packed lanes (as for the score
+ * path), one fused kernel aligns each pair and records one direction byte
+ * per band slot of every anti-diagonal it computes, then traces the path
+ * back.  With AGATHA_TB_TWO_PASS (or AGATHA_PLAIN) the score path runs
+ * first and a traceback kernel then recomputes each band up to its end
+ * cell.  AGATHA_FORCE32, a scoring beyond the 16-bit lanes, or a pair whose
+ * scores leave their range use int32 lanes (two passes).  Every form gives
+ * the same results and CIGARs.
+ * Device memory: besides the score path's buffers, a direction table of 32*C
+ * bytes per anti-diagonal (C the kernel's slots per lane for the batch's
+ * widest band: 4, 8, 16 or 24 on 16-bit lanes, up to 32 on int32 lanes),
+ * for every anti-diagonal of a pair in the fused form, up to the end cell in
+ * the two-pass form, plus about 8 bytes per base of the pair for the runs.
+ * Pairs run in waves whose tables fit in the context's budget (else in the
+ * device's free memory less min(1/16 of it, 4 GiB)); the context keeps the
+ * largest table made until agatha_destroy.
  * Errors: EINVAL (bad batch or parameters), ENOTSUP (a band wider than 1023
  * cells, or device pointers), ENOMEM (one pair's table does not fit), ERANGE,
  * ECUDA. */
