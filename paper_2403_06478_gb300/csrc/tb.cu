@@ -351,28 +351,25 @@ extern "C" int agatha_align_cigar(agatha_ctx *ctx, const agatha_batch *batch, co
             o.zdropped = 0; o.reach_end = 0; o.lane16 = 0;
             for (int k = 0; k < 5; ++k) o.pad[k] = 0;
         }
+        // handed-back pairs: an int32 two-pass traceback from their end cells,
+        // or no runs when the maximum is the origin
+        bool empty_path = false;
         for (const TbItem &it0 : items) {
             if (ncig[it0.pair] >= 0) continue;
             const agatha_result &r = out[it0.pair];
             TbItem it = it0;
             it.end_t = r.reach_end ? r.mqe_t : r.te;
             it.end_q = r.reach_end ? batch->q_len[it.pair] - 1 : r.qe;
-            if (it.end_t < 0 || it.end_q < 0) continue;   // stays n = -1: fixed below
+            if (it.end_t < 0 || it.end_q < 0) {
+                ncig[it0.pair] = 0;
+                empty_path = true;
+                continue;
+            }
             rest.push_back(it);
         }
-        // an empty path of a handed-back pair
-        for (const TbItem &it0 : items)
-            if (ncig[it0.pair] < 0) {
-                const agatha_result &r = out[it0.pair];
-                const int32_t et = r.reach_end ? r.mqe_t : r.te;
-                const int32_t eq = r.reach_end ? batch->q_len[it0.pair] - 1 : r.qe;
-                if (et < 0 || eq < 0) {
-                    const int32_t zero = 0;
-                    if ((e = cudaMemcpyAsync((int32_t *)tb.n_cigar.ptr + it0.pair, &zero, 4,
-                                             cudaMemcpyHostToDevice, s)) || (e = cudaStreamSynchronize(s)))
-                        return cuda_fail(ctx, e, "run count");
-                }
-            }
+        if (empty_path && (e = cudaMemcpyAsync(tb.n_cigar.ptr, ncig.data(), (size_t)n * 4,
+                                               cudaMemcpyHostToDevice, s)))
+            return cuda_fail(ctx, e, "run counts");
         if ((rc = run_kind(rest, K_INT32))) return rc;
     } else if (use16) {
         if ((rc = run_kind(items, K_16))) return rc;
