@@ -613,6 +613,7 @@ extern "C" int agatha_align_batch(agatha_ctx *ctx, const agatha_batch *batch,
                                   void *stream) {
     if (!ctx || !batch || !params) return AGATHA_EINVAL;
     std::lock_guard<std::mutex> lock(ctx->mu);
+    NvtxRange range("agatha_align_batch");
     DevParams p;
     if (normalise_params(params, &p)) return set_error(ctx, AGATHA_EINVAL, "bad scoring parameters");
     if (batch->n_pairs < 0) return set_error(ctx, AGATHA_EINVAL, "negative n_pairs");

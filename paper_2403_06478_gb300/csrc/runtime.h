@@ -15,6 +15,7 @@
 #include <vector>
 
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 
 #include "agatha.h"
 #include "agatha_dev.cuh"
@@ -22,6 +23,15 @@
 struct ServeState;
 
 namespace agatha {
+
+// An NVTX range for the lifetime of a scope: API calls and their phases show
+// up by name in profiler timelines (header-only NVTX 3; free without a tool).
+struct NvtxRange {
+    explicit NvtxRange(const char *name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+    NvtxRange(const NvtxRange &) = delete;
+    NvtxRange &operator=(const NvtxRange &) = delete;
+};
 
 // Device bytes a context's own buffers hold, against its budget.
 struct Ledger {

@@ -286,6 +286,7 @@ void reap(ServeState *S, ServeSlot *s) {
 // server mutex.  Returns a CUDA error; on error nothing stays enqueued that
 // would signal completion.
 cudaError_t launch_slot(ServeState *S, ServeSlot *s, const DevParams &p, int32_t max_w) {
+    NvtxRange range("serve launch");
     agatha_ctx *ctx = S->ctx;
     int64_t n = 0, qw = 0, tw = 0;
     for (const ReqPtr &r : s->reqs) {

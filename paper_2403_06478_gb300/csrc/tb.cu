@@ -155,6 +155,7 @@ extern "C" int agatha_align_cigar(agatha_ctx *ctx, const agatha_batch *batch, co
     if (flags & (AGATHA_DEVICE_PTRS | AGATHA_ASYNC))
         return set_error(ctx, AGATHA_ENOTSUP, "the traceback takes host buffers only");
     std::lock_guard<std::mutex> lock(ctx->mu);
+    NvtxRange range("agatha_align_cigar");
     DevParams p;
     if (normalise_params(params, &p)) return set_error(ctx, AGATHA_EINVAL, "bad scoring parameters");
     const int64_t n = batch->n_pairs;
@@ -263,6 +264,8 @@ extern "C" int agatha_align_cigar(agatha_ctx *ctx, const agatha_batch *batch, co
     // one kind of kernel over `list`: waves whose tables fit, each one launch
     auto run_kind = [&](std::vector<TbItem> &list, int kind) -> int {
         if (list.empty()) return AGATHA_OK;
+        NvtxRange waves(kind == K_FUSED ? "traceback waves (fused)" :
+                        (kind == K_16 ? "traceback waves (16-bit)" : "traceback waves (int32)"));
         const int C = kind == K_INT32 ? C32 : C16;
         const int64_t row = 32 * C;
         int64_t total = 0, largest = 0;
@@ -384,6 +387,7 @@ extern "C" int agatha_align_cigar(agatha_ctx *ctx, const agatha_batch *batch, co
     }
 
     // 4. layout in input order, gather, copy back
+    NvtxRange gather("CIGAR gather and copy");
     if ((e = cudaMemcpyAsync(ncig.data(), tb.n_cigar.ptr, (size_t)n * 4, cudaMemcpyDeviceToHost, s)) ||
         (e = cudaStreamSynchronize(s)))
         return cuda_fail(ctx, e, "traceback run counts");

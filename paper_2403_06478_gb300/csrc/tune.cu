@@ -108,6 +108,7 @@ constexpr float kMarginBatch = 0.99f;
 
 int tune_run(agatha_ctx *ctx, const agatha_batch *b, const DevParams &p, uint32_t flags, cudaStream_t s,
              const LaunchPlan &lp, TuneChoice *choice) {
+    NvtxRange range("autotune");
     if (!ctx->tune_ev0 && (cudaEventCreate(&ctx->tune_ev0) != cudaSuccess ||
                            cudaEventCreate(&ctx->tune_ev1) != cudaSuccess)) {
         cudaGetLastError();
