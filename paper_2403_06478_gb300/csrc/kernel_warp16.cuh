@@ -115,8 +115,9 @@ struct WarpPair16 {
     // a base window holds 2 bits per slot
     using Win = typename std::conditional<(2 * C > 32), uint64_t, uint32_t>::type;
     static constexpr Win WMASK = (Win)(((uint64_t)1 << (2 * C)) - 1);
-    // mismatch bits of a step: low-half slot p at bit 2p of lo, high-half
-    // slot p+P at bit 2p of hi (C = 24), or at bit 16+2p of lo (C <= 16)
+    // mismatch bits of a step, one word per 8 registers: register p's
+    // low-half slot p at bit 2(p mod 8), its high-half slot p+P at bit
+    // 16+2(p mod 8), of lo for p < 8 and of hi for p >= 8 (C = 24 only)
     struct Comb { uint32_t lo, hi; };
 
     // each sequence as its own words: base k of the pair at index k + phase
@@ -151,7 +152,7 @@ struct WarpPair16 {
     int32_t until_rebase;  // anti-diagonals left before the next rebase
     bool ovf;
     // packed constants
-    uint32_t A2, NB2, OEp, DOEp, Ep, E2p, NEp, NE2p, NEGp, L0LO, L31HI;
+    uint32_t A2, OEp, DOEp, Ep, E2p, NEp, NE2p, NEGp, L0LO, L31HI;
     uint32_t NABs;                 // -(a + b) as a 32-bit multiplier of the mismatch bits
     // bookkeeping (uniform across the warp)
     int32_t gmax;
@@ -220,17 +221,10 @@ struct WarpPair16 {
         if constexpr (C == 16) return {(uint32_t)nm, 0u};
         else if constexpr (C == 8) return {((uint32_t)nm & 0xffu) | (((uint32_t)nm & 0xff00u) << 8), 0u};
         else if constexpr (C == 4) return {((uint32_t)nm & 0xfu) | (((uint32_t)nm & 0xf0u) << 12), 0u};
-        else return {(uint32_t)(nm & 0xffffffu), (uint32_t)(nm >> 24)};
-    }
-    // 0xFFFF halves of register p where the slot's bases differ
-    __device__ __forceinline__ static uint32_t mismatch_mask(const Comb &c, int p) {
-        const int sh = 15 - 2 * p;
-        if constexpr (C <= 16) {
-            return prmt(c.lo << sh, 0, 0xbb99);
-        } else {
-            const uint32_t x = sh >= 0 ? c.lo << sh : c.lo >> -sh;
-            const uint32_t y = sh >= 0 ? c.hi << sh : c.hi >> -sh;
-            return prmt(x, y, 0xdd99);       // low half from bit 15 of x, high from bit 15 of y
+        else {
+            // slots 0..11 and 12..23; registers 0..7 in lo, 8..11 in hi
+            const uint32_t a = (uint32_t)(nm & 0xffffffu), b = (uint32_t)(nm >> 24);
+            return {prmt(a, b, 0x5410), prmt(a, b, 0x7632)};
         }
     }
     // 0xFFFF halves of register p from lane bits (low half p at bit p, high at 16+p)
@@ -450,17 +444,11 @@ struct WarpPair16 {
             // where the bases differ.  The first part is one multiply-add of
             // the mismatch bits: no half borrows, since every score a later
             // cell of the table can read stays far above a + b (the same
-            // argument as for the open terms below).  C = 24 keeps its
-            // bits in two words and uses the replicated-mask form.
-            uint32_t Hs, s2;
-            if constexpr (C <= 16) {
-                const uint32_t mb = (comb.lo >> (2 * p)) & 0x10001u;
-                Hs = mb * NABs + Hd[p];
-                s2 = A2;
-            } else {
-                Hs = Hd[p];
-                s2 = mux(mismatch_mask(comb, p), NB2, A2);
-            }
+            // argument as for the open terms below).
+            const uint32_t mword = (C <= 16 || p < 8) ? comb.lo : comb.hi;
+            const uint32_t mb = (mword >> (2 * (p & 7))) & 0x10001u;
+            const uint32_t Hs = mb * NABs + Hd[p];
+            const uint32_t s2 = A2;
             // H = max(H(r-2) + s, E, F, E2, F2): add-max, 3-input max, max
             const uint32_t H = __vmaxu2(__vimax3_u16x2(__viaddmax_u16x2(Hs, s2, Ein), Fin, E2in),
                                         F2in);
@@ -738,7 +726,6 @@ struct WarpPair16 {
         last_m = OFF;
         ovf = false;
         A2 = ((uint32_t)prm.a & 0xffffu) * 0x10001u;
-        NB2 = ((uint32_t)(-prm.b) & 0xffffu) * 0x10001u;
         NABs = 0u - (uint32_t)(prm.a + prm.b);
         OEp = (uint32_t)oe * 0x10001u;
         DOEp = (uint32_t)(oe2 - oe) * 0x10001u;
@@ -870,7 +857,6 @@ struct WarpPair16 {
         last_m = OFF;
         ovf = false;
         A2 = ((uint32_t)prm.a & 0xffffu) * 0x10001u;
-        NB2 = ((uint32_t)(-prm.b) & 0xffffu) * 0x10001u;
         NABs = 0u - (uint32_t)(prm.a + prm.b);
         OEp = (uint32_t)oe * 0x10001u;
         DOEp = (uint32_t)(oe2 - oe) * 0x10001u;
