@@ -51,6 +51,9 @@ WORKLOADS = {
                "zdrop=400"),
     "small": ("small: 256 pairs of 1000 bp, 5% sub / 2.5% ins / 2.5% del, a=2 b=4 q=4 e=2 "
               "q2=24 e2=1, w=100, zdrop=400"),
+    "short": ("short: 200000 pairs of 150 bp, 1% errors (0.8 sub / 0.1 ins / 0.1 del), 5% divergent "
+              "tails, BWA-MEM default parameters a=1 b=4 q=6 e=1 (single piece), w=100, zdrop=100, "
+              "end_bonus=5, this method's extension rules"),
 }
 L2_FLUSH_BYTES = 512 << 20          # > 129 MB of L2
 # algorithmic integer lane-ops per band cell (substitution score 2, five-way

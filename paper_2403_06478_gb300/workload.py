@@ -238,6 +238,13 @@ SKEWED_SCORING = Scoring(a=2, b=4, q=4, e=2, q2=24, e2=1, w=750, zdrop=400, end_
 
 CONFIG_NAMES = ("small", "ont", "hifi", "skewed")
 
+# BWA-MEM's default extension parameters (match 1, mismatch 4, gap open 6,
+# extend 1, band 100, Z-drop 100, end bonus 5): single-piece gaps, so the
+# second piece repeats the first and collapses.  Used with this method's own
+# extension rules (the paper applies its kernel to BWA-MEM, Section 5.9, but
+# states no other rule of BWA's).
+BWA_SCORING = Scoring(a=1, b=4, q=6, e=1, q2=6, e2=1, w=100, zdrop=100, end_bonus=5)
+
 
 def ont_lengths(rng: np.random.Generator, n: int) -> np.ndarray:
     x = rng.lognormal(mean=np.log(5000.0), sigma=0.8, size=n)
@@ -273,6 +280,15 @@ def make_skewed(n_pairs: int = 100_000, seed: Optional[int] = None) -> Batch:
     return _build("skewed", rng, ql, em, SKEWED_SCORING)
 
 
+def make_short(n_pairs: int = 200_000, seed: Optional[int] = None) -> Batch:
+    """Short-read extensions with BWA-MEM's default parameters: 150 bp
+    queries, 1% errors (0.8 sub / 0.1 ins / 0.1 del), 5% divergent tails."""
+    rng = np.random.default_rng(SEED_BASE + 7 if seed is None else seed)
+    ql = np.full(n_pairs, 150, dtype=np.int32)
+    em = ErrorModel(sub=0.008, ins=0.001, dele=0.001, tail_frac=0.05)
+    return _build("short", rng, ql, em, BWA_SCORING)
+
+
 def make_long_ratio(long_frac: float, n_pairs: int = 20_000, long_len: int = 4096,
                     short_len: int = 128, seed: Optional[int] = None) -> Batch:
     """Two-length mix for the load-balancing study (the paper's synthetic
@@ -292,7 +308,7 @@ def make_config(name: str, n_pairs: Optional[int] = None,
                 seed: Optional[int] = None) -> Batch:
     """Workload by name; ``n_pairs`` shrinks it (same distribution)."""
     makers = {"small": make_small, "ont": make_ont, "hifi": make_hifi,
-              "skewed": make_skewed}
+              "skewed": make_skewed, "short": make_short}
     if name not in makers:
         raise KeyError(f"unknown workload {name!r}; have {sorted(makers)}")
     if n_pairs is None:

@@ -206,6 +206,16 @@ def test_ont_full_size_sampled(ctx):
     assert A.results_equal(plain, got).size == 0
 
 
+def test_short_reads_with_bwa_parameters(ctx):
+    # 150 bp extensions with BWA-MEM's default scoring (w=100, Z-drop 100,
+    # end bonus 5): every pair of a 3,000-pair slice, batched and plain
+    batch = W.make_config("short", n_pairs=3000)
+    ref = O.align_batch(batch)
+    for path in ("batched", "plain", "force32"):
+        _assert_same(A.agatha_align_batch(ctx, batch, flags=PATHS[path]), ref, batch, f"short/{path}")
+    assert ref["reach_end"].sum() > 0          # the end bonus takes effect
+
+
 def test_hifi_full_size_sampled(ctx):
     _sampled_parity(ctx, "hifi", 120, 2)
 

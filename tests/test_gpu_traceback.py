@@ -115,7 +115,7 @@ def test_adversarial_pairs(ctx, si):
         _check(ctx, batch, f"adversarial[{si}]/{flags}", flags=flags)
 
 
-@pytest.mark.parametrize("name,n", [("ont", 120), ("hifi", 120), ("skewed", 600)])
+@pytest.mark.parametrize("name,n", [("ont", 120), ("hifi", 120), ("skewed", 600), ("short", 2000)])
 @pytest.mark.parametrize("flags", TB_FLAGS)
 def test_workload_mixes_every_pair(ctx, name, n, flags):
     batch = W.make_config(name, n_pairs=n)

@@ -47,3 +47,12 @@ def test_poisson_requests():
     sizes = np.array([len(r.pair_idx) for r in reqs])
     assert sizes.min() >= 1 and sizes.max() <= 512
     assert all((r.pair_idx >= 0).all() and (r.pair_idx < 500).all() for r in reqs)
+
+
+def test_short_read_workload():
+    b = W.make_config("short", n_pairs=2000)
+    assert b.n_pairs == 2000 and (b.q_len == 150).all()
+    assert b.scoring == W.BWA_SCORING and b.scoring.end_bonus == 5
+    assert abs(float(np.mean(b.t_len.astype(np.int64) - b.q_len))) < 1
+    again = W.make_config("short", n_pairs=2000)
+    assert np.array_equal(b.t_codes, again.t_codes)
