@@ -28,15 +28,15 @@ import argparse
 import json
 import os
 import statistics
-import subprocess
 import sys
-import tempfile
 import time
 
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 import numpy as np  # noqa: E402
+
+from paper_2403_06478_gb300.clocks import ClockSampler  # noqa: E402
 
 METRIC = "GCUPS & pairs/s on ONT-like mix: batched vs plain GPU kernel, bit-exact"
 WORKLOADS = {
@@ -76,58 +76,6 @@ def _env_int(name, default):
         return int(os.environ.get(name, default))
     except ValueError:
         return default
-
-
-class ClockSampler:
-    """nvidia-smi clocks and throttle reasons sampled every 200 ms."""
-
-    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
-             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
-             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
-
-    def __init__(self, gpu_index: int):
-        self.gpu = gpu_index
-        self.proc = None
-        self.path = None
-
-    def start(self):
-        fd, self.path = tempfile.mkstemp(prefix="clocks", suffix=".csv")
-        os.close(fd)
-        try:
-            self.proc = subprocess.Popen(
-                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.QUERY}",
-                 "--format=csv,noheader,nounits", "-lms", "200"],
-                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
-        except (OSError, FileNotFoundError):
-            self.proc = None
-
-    def stop(self):
-        if self.proc is None:
-            return None
-        self.proc.terminate()
-        try:
-            self.proc.wait(timeout=5)
-        except subprocess.TimeoutExpired:
-            self.proc.kill()
-        sm, mx, reasons = [], [], set()
-        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for line in open(self.path):
-            parts = [p.strip() for p in line.split(",")]
-            if len(parts) < 9:
-                continue
-            try:
-                sm.append(float(parts[1]))
-                mx.append(float(parts[2]))
-            except ValueError:
-                continue
-            for nm, v in zip(names, parts[5:9]):
-                if v.lower() == "active":
-                    reasons.add(nm)
-        os.unlink(self.path)
-        if not sm:
-            return None
-        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "samples": len(sm),
-                "reasons": sorted(reasons)}
 
 
 def measured_peaks():
@@ -180,7 +128,10 @@ def _kernel_digest(files=None):
     return h.hexdigest()[:16]
 
 
-def cpu_baseline(batch, n_sample: int, seed: int = 7):
+def cpu_baseline(batch, n_sample: int, gpu_res=None, seed: int = 7):
+    """The oracle on a bounded random sample of the batch, all host cores, and
+    one core on part of it.  With ``gpu_res`` (the timed step's results), the
+    sample's oracle results are also compared with them pair by pair."""
     from oracle import oracle as O      # the CPU oracle: timed here as a reported baseline
     from paper_2403_06478_gb300 import shard as S
     rng = np.random.default_rng(seed)
@@ -201,10 +152,57 @@ def cpu_baseline(batch, n_sample: int, seed: int = 7):
     res1 = O.align_batch(batch, idx=one, threads=1)
     dt1 = time.perf_counter() - t0
     cells1 = int(res1["cells"].sum())
-    return {"value": round(cells / dt / 1e9, 4), "unit": "GCUPS", "cores": cores, "kind": "oracle",
-            "sample": f"{idx.size} seeded random pairs of the workload ({cells} cells, {dt:.1f} s)",
-            "single_thread": {"value": round(cells1 / dt1 / 1e9, 4), "unit": "GCUPS", "cores": 1,
-                              "sample": f"{one.size} of those pairs ({cells1} cells, {dt1:.1f} s)"}}
+    out = {"value": round(cells / dt / 1e9, 4), "unit": "GCUPS", "cores": cores, "kind": "oracle",
+           "sample": f"{idx.size} seeded random pairs of the workload ({cells} cells, {dt:.1f} s)",
+           "single_thread": {"value": round(cells1 / dt1 / 1e9, 4), "unit": "GCUPS", "cores": 1,
+                             "sample": f"{one.size} of those pairs ({cells1} cells, {dt1:.1f} s)"}}
+    if gpu_res is not None:
+        fields = O.COMPARE_FIELDS
+        sub = gpu_res[idx]
+        bad = [int(idx[k]) for k in
+               np.flatnonzero(np.any([sub[f] != res[f] for f in fields], axis=0))]
+        out["oracle_checked_pairs"] = int(idx.size)
+        out["oracle_checked_cells"] = cells
+        out["oracle_exact"] = not bad
+        if bad:
+            out["oracle_mismatches"] = bad[:20]
+    return out
+
+
+PROFILE_PATHS = ("batched", "plain", "force32", "edge", "regs_high", "two_pass")
+
+
+def run_profile_case(args):
+    """A small case for ncu captures of one kernel (the timed benchmark is too
+    long to replay under a profiler): the first --pairs pairs of the workload
+    (or --pairs pairs of one --length: ``identical`` sequences, every
+    anti-diagonal after the first w+2 a bulk step, or ``fixed``-length pairs
+    with the small configuration's errors and ONT-like scoring), aligned
+    --repeat times on the chosen path.  Prints the cell count, not a bench line."""
+    from paper_2403_06478_gb300 import agatha as A
+    from paper_2403_06478_gb300 import build as B
+    from paper_2403_06478_gb300 import workload as W
+    flags = {"batched": 0, "plain": A.AGATHA_PLAIN, "force32": A.AGATHA_FORCE32,
+             "edge": A.AGATHA_EDGE_PATH_ONLY, "regs_high": A.AGATHA_REGS_HIGH,
+             "two_pass": A.AGATHA_TB_TWO_PASS}[args.path]
+    B.build()
+    if args.workload == "identical":
+        rng = np.random.default_rng(5)
+        xs = [rng.integers(0, 4, args.length).astype(np.uint8) for _ in range(args.pairs)]
+        batch = W.from_pairs(xs, [x.copy() for x in xs], W.ONT_SCORING, name="identical")
+    elif args.workload == "fixed":
+        batch = W.make_long_ratio(1.0, n_pairs=args.pairs, long_len=args.length)
+    else:
+        batch = W.make_config(args.workload, n_pairs=args.pairs)
+    pb = A.pack_batch(batch)
+    with A.Context(0) as ctx:
+        for _ in range(args.repeat):
+            if args.traceback:
+                res, _, _ = ctx.align_cigar(pb, batch.scoring, flags=flags)
+            else:
+                res = ctx.align_host(pb, batch.scoring, flags=flags)
+    print(f"ok {args.workload} pairs={batch.n_pairs} cells={int(res['cells'].sum())}")
+    return 0
 
 
 def run_reference(args):
@@ -413,12 +411,25 @@ def main():
     ap.add_argument("--cpu-sample-pairs", type=int, default=CPU_SAMPLE_PAIRS)
     ap.add_argument("--tune-cache", default=None,
                     help="autotuner cache file: read if present, written after tuning")
-    ap.add_argument("--workload", default="ont", choices=sorted(WORKLOADS),
-                    help="ont (the headline), or another configuration of the same metric")
+    ap.add_argument("--workload", default="ont", choices=sorted(WORKLOADS) + ["identical", "fixed"],
+                    help="ont (the headline), or another configuration of the same metric "
+                         "(identical / fixed: --profile-case only)")
+    ap.add_argument("--profile-case", action="store_true",
+                    help="run a small case for an ncu capture instead of the benchmark")
+    ap.add_argument("--pairs", type=int, default=2000, help="--profile-case: pairs")
+    ap.add_argument("--repeat", type=int, default=2, help="--profile-case: calls")
+    ap.add_argument("--length", type=int, default=20000,
+                    help="--profile-case: pair length of --workload identical / fixed")
+    ap.add_argument("--path", default="batched", choices=PROFILE_PATHS,
+                    help="--profile-case: kernel path")
     ap.add_argument("--traceback", action="store_true",
                     help="the path with CIGARs: score kernels + traceback kernel")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
+    if args.profile_case:
+        return run_profile_case(args)
+    if args.workload not in WORKLOADS:
+        ap.error(f"--workload {args.workload} is only for --profile-case")
     if args.impl == "reference":
         return run_reference(args)
     if args.traceback:
@@ -578,7 +589,9 @@ def main():
         "clocks": clocks,
     }
     if world == 1 and not args.no_cpu_baseline:
-        line["cpu_baseline"] = cpu_baseline(batch, args.cpu_sample_pairs)
+        line["cpu_baseline"] = cpu_baseline(batch, args.cpu_sample_pairs, gpu_res=res)
+        line["oracle_exact"] = line["cpu_baseline"]["oracle_exact"]
+        line["oracle_checked_pairs"] = line["cpu_baseline"]["oracle_checked_pairs"]
     print(json.dumps(line), flush=True)
     ctx.close()
     if dist is not None:

@@ -71,6 +71,9 @@ extern "C" {
 #define AGATHA_NO_TUNE     0x100u /* ignore the autotuner for this call       */
 #define AGATHA_TB_TWO_PASS 0x200u /* agatha_align_cigar: score path, then a
                                      separate traceback pass (not fused)    */
+#define AGATHA_WARPS2      0x400u /* 16-bit kernel with 2 warps sharing each
+                                     pair's band (bands of 256..767 slots)   */
+#define AGATHA_WARPS4      0x800u /* the same with 4 warps per pair           */
 
 /* Flags for agatha_config.flags. */
 #define AGATHA_CFG_TIMING  0x1    /* record CUDA events around the main kernel
@@ -310,6 +313,14 @@ typedef struct {
     int64_t bytes_in_flight, peak_bytes_in_flight;
     double busy_seconds;        /* wall time with work on the device        */
     double p50_latency_ms, p99_latency_ms;
+    /* Overlap of launches.  max_launches_in_flight: the most launches that
+     * were enqueued and not yet retired at one time (host view).  From the
+     * device's global timer, per finished launch, the span from the first
+     * block of its first kernel to the last warp of its alignment kernels:
+     * max_device_concurrency is the most spans covering one instant and
+     * overlap_seconds the device time covered by two or more spans. */
+    int64_t max_launches_in_flight, max_device_concurrency;
+    double overlap_seconds;
 } agatha_serve_stats;
 
 /* Start the scheduler thread of ctx (one server per context).  EINVAL on a
@@ -362,11 +373,16 @@ int agatha_serve_stop(agatha_ctx *ctx, int32_t drain);
  *          for its work on that stream before returning.
  * The first call on a device looks up the array's device address and
  * prepares the kernels; make that first call before any stream capture.
+ * Every call copies its batch descriptor from host memory into the array and
+ * then waits for the stream, so it returns only after the results are written.
  * All calls share the one array and it keeps the last call's contents (the
  * call clears what must start at zero): calls whose work overlaps on the GPU
  * (other streams or host threads) race, so the caller must serialise them.
- * Errors: EINVAL (n_pairs > AGATHA_NOALLOC_MAX_PAIRS, bad parameters, a pair
- * outside its stream), ENOTSUP (band wider than supported), ECUDA. */
+ * Errors: EINVAL (n_pairs > AGATHA_NOALLOC_MAX_PAIRS, bad parameters, a null
+ * array the pairs need - q_packed with q_words > 0, t_packed with t_words > 0,
+ * lengths, offsets or out -, a pair outside its stream: that pair's record is
+ * written empty and the others are aligned), ENOTSUP (band wider than
+ * supported), ECUDA. */
 #define AGATHA_NOALLOC_MAX_PAIRS 65536
 int agatha_align_batch_noalloc(const agatha_batch *batch, const agatha_params *params,
                                agatha_result *out, void *stream);

@@ -40,6 +40,8 @@ AGATHA_EDGE_PATH_ONLY = 0x40
 AGATHA_REGS_HIGH = 0x80
 AGATHA_NO_TUNE = 0x100
 AGATHA_TB_TWO_PASS = 0x200
+AGATHA_WARPS2 = 0x400
+AGATHA_WARPS4 = 0x800
 
 AGATHA_CFG_TIMING = 0x1
 AGATHA_CFG_AUTOTUNE = 0x2
@@ -51,7 +53,7 @@ AGATHA_CIGAR_D = 2
 CIGAR_OPS = "MID"
 
 # kernel variants the autotuner chooses between, per length class
-VARIANT_NAMES = ("int16x2", "int16x2-highreg", "int32")
+VARIANT_NAMES = ("int16x2", "int16x2-highreg", "int32", "int16x2-2warps", "int16x2-4warps")
 
 NEG_INF = -0x40000000
 
@@ -103,7 +105,8 @@ class agatha_serve_stats(ctypes.Structure):
                 ("cells_done", ctypes.c_int64), ("launches", ctypes.c_int64),
                 ("bytes_in_flight", ctypes.c_int64), ("peak_bytes_in_flight", ctypes.c_int64),
                 ("busy_seconds", ctypes.c_double), ("p50_latency_ms", ctypes.c_double),
-                ("p99_latency_ms", ctypes.c_double)]
+                ("p99_latency_ms", ctypes.c_double), ("max_launches_in_flight", ctypes.c_int64),
+                ("max_device_concurrency", ctypes.c_int64), ("overlap_seconds", ctypes.c_double)]
 
 
 class agatha_tb_info(ctypes.Structure):
@@ -377,9 +380,12 @@ AGATHA_NOALLOC_MAX_PAIRS = 65536
 
 
 def agatha_align_batch_noalloc(q_packed, t_packed, q_off, t_off, q_len, t_len, out, scoring,
-                               stream: int = 0, n_pairs: Optional[int] = None) -> None:
+                               stream: int = 0, n_pairs: Optional[int] = None,
+                               words: Optional[tuple] = None) -> None:
     """The allocation-free entry point on device tensors (torch CUDA tensors or
-    raw pointers).  ``out`` holds n_pairs * 48 bytes of device memory."""
+    raw pointers).  ``out`` holds n_pairs * 48 bytes of device memory;
+    ``words`` = (q_words, t_words) overrides the stream sizes taken from the
+    tensors."""
     def ptr(x):
         if x is None:
             return None
@@ -389,7 +395,8 @@ def agatha_align_batch_noalloc(q_packed, t_packed, q_off, t_off, q_len, t_len, o
         return 0 if x is None else (int(x.numel()) if hasattr(x, "numel") else int(len(x)))
 
     n = numel(q_len) if n_pairs is None else int(n_pairs)
-    b = agatha_batch(n, ptr(q_packed), ptr(t_packed), numel(q_packed), numel(t_packed),
+    qw, tw = words if words is not None else (numel(q_packed), numel(t_packed))
+    b = agatha_batch(n, ptr(q_packed), ptr(t_packed), qw, tw,
                      ptr(q_off), ptr(t_off), ptr(q_len), ptr(t_len))
     p = make_params(scoring)
     _check(lib().agatha_align_batch_noalloc(ctypes.byref(b), ctypes.byref(p),

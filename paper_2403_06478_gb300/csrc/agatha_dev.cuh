@@ -55,7 +55,28 @@ struct DevBatch {
 };
 
 enum : int32_t { CTR_HEAD = 0, CTR_NWARP = 1, CTR_NWIDE = 2, CTR_ERR = 3, CTR_WIDE_HEAD = 4,
-                 CTR_NOVF = 5, CTR_OVF_HEAD = 6, CTR_CLS_HEAD = 8, CTR_COUNT = 12 };
+                 CTR_NOVF = 5, CTR_OVF_HEAD = 6, CTR_CLS_HEAD = 8, CTR_T_BEGIN = 12, CTR_T_END = 14,
+                 CTR_COUNT = 16 };
+
+// Device clock of a step's kernels, in nanoseconds of the GPU's global timer
+// (one clock for every SM): counters[CTR_T_BEGIN..+1] holds when the first
+// block of the step's first kernel started, counters[CTR_T_END..+1] when the
+// last warp of its alignment kernels finished.  Both are 64-bit words inside
+// the counters, so they are cleared with them at the start of every step.
+// The serving loop reads them to tell whether two launches ran at once.
+__device__ __forceinline__ uint64_t global_ns() {
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+__device__ __forceinline__ void mark_step_begin(int32_t *counters) {
+    atomicCAS(reinterpret_cast<unsigned long long *>(counters + CTR_T_BEGIN), 0ull,
+              (unsigned long long)global_ns());
+}
+__device__ __forceinline__ void mark_step_end(int32_t *counters) {
+    atomicMax(reinterpret_cast<unsigned long long *>(counters + CTR_T_END),
+              (unsigned long long)global_ns());
+}
 
 // Which pair list a warp kernel launch walks: the whole ordered queue, the
 // pairs the 16-bit kernel handed back, or the part of the ordered queue that
@@ -225,6 +246,11 @@ cudaError_t launch_warp16_c(const DevBatch *d_batch, int n_blocks, cudaStream_t 
                             int list = WARP_LIST_MAIN);
 template <int C, int MINB>
 int occupancy_warp16_c();
+// K warps share one pair's band (C slots per lane of each warp).
+template <int C, int K, int MINB>
+cudaError_t launch_warp16k_c(const DevBatch *d_batch, int n_blocks, cudaStream_t s, int use_fast, int list);
+template <int C, int K, int MINB>
+int occupancy_warp16k_c();
 template <int C>
 cudaError_t launch_tb_c(const DevBatch *d_batch, const TbItem *items, int32_t n_items, int32_t *head,
                         uint8_t *dir, uint32_t *ops, int32_t *n_cigar, int n_blocks, cudaStream_t s);

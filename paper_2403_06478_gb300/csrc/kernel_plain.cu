@@ -174,6 +174,7 @@ plain_align_kernel(const DevBatch *__restrict__ d_batch, int32_t slots, int32_t 
         }
         __syncthreads();
     }
+    if (threadIdx.x == 0) mark_step_end(Bt.counters);
 }
 
 static size_t plain_smem_bytes(int32_t slots) {

@@ -28,6 +28,7 @@ __device__ __forceinline__ int32_t work_bucket(int32_t tlen, int32_t qlen, int32
 
 __global__ void prep_classify_kernel(const DevBatch *__restrict__ d_batch, int32_t sort) {
     const DevBatch B = *d_batch;
+    if (threadIdx.x == 0) mark_step_begin(B.counters);
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < B.n_pairs;
          i += (int64_t)gridDim.x * blockDim.x) {
         if (!pair_valid(B, i)) {

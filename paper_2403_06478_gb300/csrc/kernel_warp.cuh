@@ -443,6 +443,7 @@ warp_align_kernel(const DevBatch *__restrict__ d_batch, int32_t use_fast, int32_
         WarpPair<C> wp;
         wp.run(B, pair, lane, use_fast != 0);
     }
+    if (lane == 0) mark_step_end(B.counters);
 }
 
 template <int C>

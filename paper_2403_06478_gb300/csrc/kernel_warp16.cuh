@@ -88,6 +88,20 @@ struct Cold16 {
     int64_t cells;
 };
 
+// What the K warps sharing one pair's band (K > 1) hand each other through
+// shared memory after every anti-diagonal, double-buffered by its parity:
+// the gap-state word a warp's edge lane publishes for the neighbouring warp
+// (E/E2 of its last slot going up, or F/F2 of its first slot going down), the
+// warp's anti-diagonal maximum, and overflow flags.
+struct Xchg16 {
+    uint32_t e0[2][4], e1[2][4];
+    int32_t m[2][4];
+    int32_t f[2][4];
+    int32_t t[2];                 // cell (t) of the maximum, found by the warp holding it
+    int32_t g[4];                 // flags of a group-wide vote
+    int32_t pair;                 // the group's current pair
+};
+
 // DMREG: keep the dead-slot masks in registers (the larger register budget)
 // instead of recomputing them at every use.  DEFER: a new maximum found by a
 // bulk step is only located (its cell found) when that can matter: before the
@@ -108,10 +122,18 @@ struct Cold16 {
 // direction bytes of every anti-diagonal it computes, so the traceback needs
 // no second pass over the band; without SCORE (run_dir) the end anti-diagonal
 // is given and nothing else is tracked.
-template <int C, bool DMREG, bool DEFER = false, bool DIR = false, bool SCORE = !DIR>
+// K: warps sharing one pair's band (1, 2 or 4).  Warp k of the group holds
+// slots 32kC .. 32(k+1)C - 1 of the frame; after every anti-diagonal the warps
+// exchange their edge gap states and anti-diagonal maxima through shared
+// memory and a named barrier, so that the termination test stays exact.
+template <int C, bool DMREG, bool DEFER = false, bool DIR = false, bool SCORE = !DIR, int K = 1>
 struct WarpPair16 {
-    static_assert(C == 4 || C == 8 || C == 16 || C == 24, "16-bit lanes use 4, 8, 16 or 24 slots per lane");
+    static_assert(C == 4 || C == 6 || C == 8 || C == 12 || C == 16 || C == 24,
+                  "16-bit lanes use 4, 6, 8, 12, 16 or 24 slots per lane");
+    static_assert(K == 1 || K == 2 || K == 4, "1, 2 or 4 warps per pair");
+    static_assert(K == 1 || !DIR, "the traceback variants run one warp per pair");
     static constexpr int P = C / 2;
+    static constexpr int32_t NS = 32 * C * K;     // slots of the frame
     // a base window holds 2 bits per slot
     using Win = typename std::conditional<(2 * C > 32), uint64_t, uint32_t>::type;
     static constexpr Win WMASK = (Win)(((uint64_t)1 << (2 * C)) - 1);
@@ -160,8 +182,81 @@ struct WarpPair16 {
     // state the bulk step never reads, kept in shared memory (written by lane
     // 0) so that it holds no registers through the bulk loop
     Cold16 &cold;
+    // K > 1: this warp's place in the group, the group's exchange area and
+    // named barrier, the edge words the neighbouring warp published for the
+    // next anti-diagonal, and this warp's maximum at the last exchange
+    Xchg16 *xch;
+    int32_t wk, bar_id;
+    uint32_t xe0, xe1;
+    int32_t xm_w;
+    int32_t pend_owner;            // K > 1: the warp holding the pending maximum
 
-    __device__ explicit WarpPair16(Cold16 &c) : cold(c) {}
+    __device__ explicit WarpPair16(Cold16 &c, Xchg16 *x = nullptr, int32_t wk_ = 0, int32_t bar = 0)
+        : cold(c), xch(x), wk(wk_), bar_id(bar) {}
+
+    // K > 1: barrier of the group's warps (orders their shared-memory traffic)
+    __device__ __forceinline__ void group_sync() const {
+        if constexpr (K == 4) {
+            asm volatile("bar.sync 1, 128;" ::: "memory");
+        } else if constexpr (K == 2) {
+            if (bar_id == 1) asm volatile("bar.sync 1, 64;" ::: "memory");
+            else asm volatile("bar.sync 2, 64;" ::: "memory");
+        }
+    }
+    // the lane that publishes for the group (lane 0 of warp 0)
+    __device__ __forceinline__ bool leader() const { return lane == 0 && (K == 1 || wk == 0); }
+    // K > 1: true in every lane of the group if v is true in any lane of any warp
+    __device__ __forceinline__ bool group_any(bool v) {
+        const bool w_any = __any_sync(FULL, v);
+        if constexpr (K == 1) return w_any;
+        if (lane == 0) xch->g[wk] = w_any ? 1 : 0;
+        group_sync();
+        int32_t a = 0;
+#pragma unroll
+        for (int k = 0; k < K; ++k) a |= xch->g[k];
+        group_sync();
+        return a != 0;
+    }
+    // K > 1: publish this warp's anti-diagonal maximum lm (lane maxima) and,
+    // for the next anti-diagonal (odd one when ODDNEXT), the edge gap states
+    // the neighbouring warp needs; with FLAG also the overflow flag.  Returns
+    // the group's maximum; leaves the neighbour's edge words in xe0/xe1.
+    template <bool ODDNEXT, bool FLAG>
+    __device__ __forceinline__ int32_t exchange(int32_t r, int32_t lm) {
+        const int b = r & 1;
+        const int32_t mw = __reduce_max_sync(FULL, lm);
+        const bool fw = FLAG ? __any_sync(FULL, ovf) : false;
+        if (lane == 0) {
+            xch->m[b][wk] = mw;
+            if (FLAG) xch->f[b][wk] = fw ? 1 : 0;
+        }
+        if (ODDNEXT) {
+            if (lane == 31) { xch->e0[b][wk] = Eo[P - 1]; xch->e1[b][wk] = E2o[P - 1]; }
+        } else {
+            if (lane == 0) { xch->e0[b][wk] = Fo[0]; xch->e1[b][wk] = F2o[0]; }
+        }
+        group_sync();
+        int32_t m = xch->m[b][0];
+        int32_t f = FLAG ? xch->f[b][0] : 0;
+#pragma unroll
+        for (int k = 1; k < K; ++k) {
+            m = max(m, xch->m[b][k]);
+            if (FLAG) f |= xch->f[b][k];
+        }
+        if (FLAG) ovf = f != 0;
+        const int src = ODDNEXT ? wk - 1 : wk + 1;
+        if (src >= 0 && src < K) { xe0 = xch->e0[b][src]; xe1 = xch->e1[b][src]; }
+        xm_w = mw;
+        return m;
+    }
+    // K > 1: the lowest warp whose maximum at the last exchange of r is m
+    __device__ __forceinline__ int32_t owner_of(int32_t r, int32_t m) const {
+        const int b = r & 1;
+        int32_t o = K - 1;
+#pragma unroll
+        for (int k = K - 1; k >= 0; --k) o = xch->m[b][k] == m ? k : o;
+        return o;
+    }
 
     __device__ __forceinline__ int32_t to_true(int32_t u) const { return u - OFF + base; }
     __device__ __forceinline__ int32_t to_u(int32_t v) const { return v - base + OFF; }
@@ -219,7 +314,9 @@ struct WarpPair16 {
         const Win x = Tw ^ Qw;
         const Win nm = (x | (x >> 1)) & (Win)0x5555555555555555ull;    // slot jl at bit 2*jl
         if constexpr (C == 16) return {(uint32_t)nm, 0u};
+        else if constexpr (C == 12) return {((uint32_t)nm & 0xfffu) | (((uint32_t)nm & 0xfff000u) << 4), 0u};
         else if constexpr (C == 8) return {((uint32_t)nm & 0xffu) | (((uint32_t)nm & 0xff00u) << 8), 0u};
+        else if constexpr (C == 6) return {((uint32_t)nm & 0x3fu) | (((uint32_t)nm & 0xfc0u) << 10), 0u};
         else if constexpr (C == 4) return {((uint32_t)nm & 0xfu) | (((uint32_t)nm & 0xf0u) << 12), 0u};
         else {
             // slots 0..11 and 12..23; registers 0..7 in lo, 8..11 in hi
@@ -267,7 +364,7 @@ struct WarpPair16 {
         const int32_t qstar = r - tstar;
         if (m > gmax) {
             gmax = m;
-            if (lane == 0) { cold.gt = tstar; cold.gq = qstar; }
+            if (leader()) { cold.gt = tstar; cold.gq = qstar; }
             __syncwarp();
             return false;
         }
@@ -289,6 +386,11 @@ struct WarpPair16 {
     __device__ __forceinline__ void locate_pending() {
         if constexpr (DEFER) {
             if (pend_r == -3) return;
+            if (K > 1 && wk != pend_owner) {       // the warp holding it finds it
+                group_sync();
+                pend_r = -3;
+                return;
+            }
             const unsigned ball = __ballot_sync(FULL, pend_lm == pend_m);
             const int src = __ffs(ball) - 1;
             const uint32_t mh2 = (uint32_t)(pend_m + oe) * 0x10001u;
@@ -300,18 +402,19 @@ struct WarpPair16 {
             const uint32_t lo_eq = eq & 0xffffu, hi_eq = eq >> 16;
             const int32_t jl = lo_eq ? __ffs(lo_eq) - 1 : P + __ffs(hi_eq) - 1;
             const int32_t lj = __shfl_sync(FULL, jl, src);
-            const int32_t tstar = frame(pend_r) + src * C + lj;
+            const int32_t tstar = frame(pend_r) + (wk * 32 + src) * C + lj;
             if (lane == 0) { cold.gt = tstar; cold.gq = pend_r - tstar; }
             __syncwarp();
+            group_sync();
             pend_r = -3;
         }
     }
 
+    // lm: the lane's maximum; m_grp (K > 1): the group's, from exchange().
     template <bool ODD, typename Excl, bool BULKSTEP = false>
-    __device__ __forceinline__ bool anti_diagonal_max(int32_t r, int32_t B, uint32_t lmax,
+    __device__ __forceinline__ bool anti_diagonal_max(int32_t r, int32_t B, int32_t lm, int32_t m_grp,
                                                       const uint32_t (&Hn)[P], Excl excl) {
-        const int32_t lm = (int32_t)max(lmax & 0xffffu, lmax >> 16);
-        const int32_t m = __reduce_max_sync(FULL, lm);
+        const int32_t m = K == 1 ? __reduce_max_sync(FULL, lm) : m_grp;
         const int32_t mt = to_true(m + oe);
         last_m = m + oe;
         if constexpr (DEFER && BULKSTEP) {
@@ -320,8 +423,9 @@ struct WarpPair16 {
 #pragma unroll
                 for (int p = 0; p < P; ++p) Hsave[p] = Hn[p];
                 pend_r = r;
-                pend_m = m;
+                pend_m = K == 1 ? m : xm_w;
                 pend_lm = lm;
+                if constexpr (K > 1) pend_owner = owner_of(r, m);
                 return false;
             }
             if (!(prm.zdrop >= 0 && gmax - mt > prm.zdrop)) return false;
@@ -329,19 +433,29 @@ struct WarpPair16 {
         }
         if (mt > gmax || (prm.zdrop >= 0 && gmax - mt > prm.zdrop)) {
             // position only when it can matter: lowest slot of the first lane
-            // holding the maximum; bit p / 16+p of `ne` is set where the low /
-            // high half of register p is not it
-            const unsigned ball = __ballot_sync(FULL, lm == m);
-            const int src = __ffs(ball) - 1;
-            const uint32_t mh2 = (uint32_t)(m + oe) * 0x10001u;
-            uint32_t ne = 0;
+            // (of the first warp) holding the maximum; bit p / 16+p of `ne` is
+            // set where the low / high half of register p is not it
+            int32_t tstar = 0;
+            const int32_t owner = K == 1 ? 0 : owner_of(r, m);
+            if (K == 1 || wk == owner) {
+                const unsigned ball = __ballot_sync(FULL, lm == m);
+                const int src = __ffs(ball) - 1;
+                const uint32_t mh2 = (uint32_t)(m + oe) * 0x10001u;
+                uint32_t ne = 0;
 #pragma unroll
-            for (int p = 0; p < P; ++p) ne += __vminu2((Hn[p] ^ mh2) | excl(p), 0x10001u) << p;
-            const uint32_t eq = ~ne & ((((1u << P) - 1) << 16) | ((1u << P) - 1));
-            const uint32_t lo_eq = eq & 0xffffu, hi_eq = eq >> 16;
-            const int32_t jl = lo_eq ? __ffs(lo_eq) - 1 : P + __ffs(hi_eq) - 1;
-            const int32_t lj = __shfl_sync(FULL, jl, src);
-            if (max_and_zdrop(mt, B + src * C + lj, r)) { zdropped = 1; return true; }
+                for (int p = 0; p < P; ++p) ne += __vminu2((Hn[p] ^ mh2) | excl(p), 0x10001u) << p;
+                const uint32_t eq = ~ne & ((((1u << P) - 1) << 16) | ((1u << P) - 1));
+                const uint32_t lo_eq = eq & 0xffffu, hi_eq = eq >> 16;
+                const int32_t jl = lo_eq ? __ffs(lo_eq) - 1 : P + __ffs(hi_eq) - 1;
+                const int32_t lj = __shfl_sync(FULL, jl, src);
+                tstar = B + (wk * 32 + src) * C + lj;
+                if (K > 1 && lane == 0) xch->t[r & 1] = tstar;
+            }
+            if constexpr (K > 1) {
+                group_sync();
+                tstar = xch->t[r & 1];
+            }
+            if (max_and_zdrop(mt, tstar, r)) { zdropped = 1; return true; }
         }
         return false;
     }
@@ -354,8 +468,10 @@ struct WarpPair16 {
 #pragma unroll
         for (int p = 1; p < P; ++p) v = pl == p ? Hn[p] : v;
         const int32_t h = local >= P ? (int32_t)(v >> 16) : (int32_t)(v & 0xffffu);
-        return __shfl_sync(FULL, h, j / C);
+        return __shfl_sync(FULL, h, (j / C) & 31);
     }
+    // K > 1: the warp of the group that holds frame slot j
+    __device__ __forceinline__ static int32_t slot_warp(int32_t j) { return j / (32 * C); }
 
     // Step modes.  BULK: every slot in [0, w] is a band cell of the table.
     // HEAD (r <= w + 1): the band meets the table's first row and column;
@@ -399,19 +515,24 @@ struct WarpPair16 {
         if constexpr (ODD) {
             // E of slot 0 from the left lane's last slot (high half of its last
             // register); for lane 0 it would feed slot 0, outside the band here
-            const uint32_t eL = __shfl_up_sync(FULL, Eo[P - 1], 1);
-            const uint32_t e2L = __shfl_up_sync(FULL, E2o[P - 1], 1);
+            // (with K warps, lane 0 of a later warp takes the word the warp
+            // below published)
+            uint32_t eL = __shfl_up_sync(FULL, Eo[P - 1], 1);
+            uint32_t e2L = __shfl_up_sync(FULL, E2o[P - 1], 1);
+            if (K > 1 && wk > 0 && lane == 0) { eL = xe0; e2L = xe1; }
             edge = mux(L0LO, NEGp, prmt(eL, Eo[P - 1], 0x5432));
             edge2 = mux(L0LO, NEGp, prmt(e2L, E2o[P - 1], 0x5432));
         } else {
-            // F of the last slot from the right lane's first slot (low half of its register 0)
-            const uint32_t fR = __shfl_down_sync(FULL, Fo[0], 1);
-            const uint32_t f2R = __shfl_down_sync(FULL, F2o[0], 1);
+            // F of the last slot from the right lane's first slot (low half of
+            // its register 0; with K warps, from the warp above for lane 31)
+            uint32_t fR = __shfl_down_sync(FULL, Fo[0], 1);
+            uint32_t f2R = __shfl_down_sync(FULL, F2o[0], 1);
+            if (K > 1 && wk < K - 1 && lane == 31) { fR = xe0; f2R = xe1; }
             uint32_t inj = NEGp, inj2 = NEGp;
-            if (MODE == HEAD && lane == 31) {
-                // beyond the last lane: slot 32C of r-1, the virtual column
+            if (MODE == HEAD && lane == 31 && (K == 1 || wk == K - 1)) {
+                // beyond the last lane: slot NS of r-1, the virtual column
                 // cell (t, -1) when q == -1 there
-                const int32_t ts = frame(r - 1) + 32 * C, qs = r - 1 - ts;
+                const int32_t ts = frame(r - 1) + NS, qs = r - 1 - ts;
                 if (qs == -1 && ts >= 0 && ts < tlen) {
                     const int32_t v = to_u(-gap_cost(prm, ts + 1));
                     if (v < cold.LOWCHK || v > 0xffff - cold.Dp) ovf = true;
@@ -503,31 +624,35 @@ struct WarpPair16 {
         if constexpr (DIR && SCORE) {
             if (r >= 0) store_row(r, dbits);
         }
+        const int32_t lm = (int32_t)max(lmax & 0xffffu, lmax >> 16);
+        int32_t m_grp = 0;
+        if constexpr (K > 1) m_grp = exchange<!ODD, MODE != BULK>(r, lm);
         if constexpr (MODE == BULK) {
             // (the band cells of bulk anti-diagonals are counted by run())
             // slots beyond the band sit above every band slot of their lane, so
             // the lowest slot holding the maximum is a band slot; only slot 0 of
             // lane 0 (below the band on odd anti-diagonals) is excluded
             auto excl = [&](int p) { return (ODD && p == 0) ? L0LO : 0u; };
-            return anti_diagonal_max<ODD, decltype(excl), true>(r, B, lmax, Hd, excl);
+            return anti_diagonal_max<ODD, decltype(excl), true>(r, B, lm, m_grp, Hd, excl);
         } else {
-            if (__any_sync(FULL, ovf)) { ovf = true; return true; }
+            if (K == 1 ? __any_sync(FULL, ovf) : ovf) { ovf = true; return true; }
             if (r < 0) return false;
-            if (lane == 0) cold.cells += en - st + 1;
-            // best score on the last target row / the last query column
+            if (leader()) cold.cells += en - st + 1;
+            // best score on the last target row / the last query column (with
+            // K warps, the warp holding the slot reads it)
             bool set_gs = false;
             int32_t gs = K_NEG_OUT;
-            if (st <= tlen - 1 && tlen - 1 <= en) {
+            if (st <= tlen - 1 && tlen - 1 <= en && (K == 1 || slot_warp(tlen - 1 - B) == wk)) {
                 const int32_t tv = to_true(slot_value(Hd, tlen - 1 - B));
                 if (tv > cold.mte && lane == 0) { cold.mte = tv; cold.mte_q = r - (tlen - 1); }
                 if (r == last_r) { gs = tv; set_gs = true; }   // kept unless Z-drop stops r
             }
-            if (st <= r - qlen + 1 && r - qlen + 1 <= en) {
+            if (st <= r - qlen + 1 && r - qlen + 1 <= en && (K == 1 || slot_warp(r - qlen + 1 - B) == wk)) {
                 const int32_t qv = to_true(slot_value(Hd, r - qlen + 1 - B));
                 if (qv > cold.mqe && lane == 0) { cold.mqe = qv; cold.mqe_t = r - (qlen - 1); }
             }
             __syncwarp();
-            if (anti_diagonal_max<ODD>(r, B, lmax, Hd, [&](int p) { return ~half_mask_rt(rb, p); }))
+            if (anti_diagonal_max<ODD>(r, B, lm, m_grp, Hd, [&](int p) { return ~half_mask_rt(rb, p); }))
                 return true;
             if (set_gs && lane == 0) cold.gscore = gs;
             if (--until_rebase <= 2) {
@@ -645,7 +770,7 @@ struct WarpPair16 {
         if (delta >= 0) rebase_all<true>((uint32_t)min(delta, 0xffff) * 0x10001u, low2, odd, in_ev, in_od);
         else rebase_all<false>((uint32_t)min(-delta, 0xffff) * 0x10001u, low2, odd, in_ev, in_od);
         base += delta;
-        if (__any_sync(FULL, ovf)) ovf = true;
+        ovf = group_any(ovf);
     }
     template <bool SUB>
     __device__ __forceinline__ void rebase_all(uint32_t d2, uint32_t low2, bool odd, uint32_t in_ev,
@@ -663,6 +788,22 @@ struct WarpPair16 {
             rebase_reg<SUB>(Fo[p], dm_r, d2, low2);
             rebase_reg<SUB>(F2o[p], dm_r, d2, low2);
         }
+        if constexpr (K > 1) {
+            // the edge words the neighbouring warp published before this
+            // rebase move with the rest (the half the next anti-diagonal reads:
+            // high for an odd one, low for an even one); the neighbour checks
+            // its own copy, so these are only shifted
+            const bool next_odd = !odd;
+            const uint32_t keep = next_odd ? 0xffff0000u : 0x0000ffffu;
+            rebase_edge<SUB>(xe0, keep, d2);
+            rebase_edge<SUB>(xe1, keep, d2);
+        }
+    }
+    template <bool SUB>
+    __device__ __forceinline__ void rebase_edge(uint32_t &x, uint32_t keep, uint32_t d2) const {
+        const uint32_t reset = __vcmpleu2(x, NEGp) | ~keep;
+        const uint32_t y = __vmaxu2(SUB ? __vsubus2(x, d2) : __vaddus2(x, d2), NEGp + 0x10001u);
+        x = mux(reset, NEGp, y);
     }
     // lane bits of the virtual row/column cells among the slots of anti-diagonal r
     __device__ __forceinline__ uint32_t virtual_bits(int32_t r) const {
@@ -704,19 +845,19 @@ struct WarpPair16 {
         agatha_result *out = Bt.out + pair;
         if constexpr (DIR) { end_t = -1; end_q = -1; }
         if (tlen <= 0 || qlen <= 0) {
-            if (lane == 0) write_empty_result(out);
+            if (leader()) write_empty_result(out);
             return true;
         }
         w = effective_w(prm.w, tlen, qlen);
         oe = prm.q + prm.e; oe2 = prm.q2 + prm.e2;
-        j0 = lane * C;
+        j0 = (wk * 32 + lane) * C;
         last_r = tlen + qlen - 2;
         if constexpr (DIR) dtab = dt + j0;
         {
             const int32_t Dp = step_change_max(prm), kint = rebase_interval(Dp);
             until_rebase = kint;
             OFF = 0xffff - (kint + 3) * Dp;
-            if (lane == 0) {
+            if (leader()) {
                 cold.Dp = Dp;
                 cold.kint = kint;
                 cold.LOWCHK = (int32_t)U_NEG + (kint + 3) * Dp;
@@ -734,8 +875,9 @@ struct WarpPair16 {
         NEp = ((uint32_t)(-prm.e) & 0xffffu) * 0x10001u;
         NE2p = ((uint32_t)(-prm.e2) & 0xffffu) * 0x10001u;
         NEGp = U_NEG * 0x10001u;
-        L0LO = lane == 0 ? 0x0000ffffu : 0u;
-        L31HI = lane == 31 ? 0xffff0000u : 0u;
+        L0LO = (lane == 0 && wk == 0) ? 0x0000ffffu : 0u;
+        L31HI = (lane == 31 && wk == K - 1) ? 0xffff0000u : 0u;
+        xe0 = xe1 = NEGp;
 #pragma unroll
         for (int p = 0; p < P; ++p) {
             Hev[p] = Hod[p] = Eo[p] = E2o[p] = Fo[p] = F2o[p] = NEGp;
@@ -751,13 +893,14 @@ struct WarpPair16 {
         }
         gmax = 0;
         pend_r = -3;
-        if (lane == 0) {
+        if (leader()) {
             cold.mqe = K_NEG_OUT; cold.mqe_t = -1; cold.mte = K_NEG_OUT; cold.mte_q = -1;
             cold.gscore = K_NEG_OUT;
             cold.gt = -1; cold.gq = -1;
             cold.cells = 0;
         }
         __syncwarp();
+        group_sync();
         zdropped = 0;
 
         int32_t r = -2;
@@ -788,7 +931,7 @@ struct WarpPair16 {
             // every bulk anti-diagonal holds the whole band: w + 1 cells when
             // (r - w) is even, w when it is odd; the first one is even
             const int32_t nb = r - r0;
-            if (lane == 0) cold.cells += (int64_t)(nb >> 1) * (2 * w + 1) + (int64_t)(nb & 1) * (w + 1);
+            if (leader()) cold.cells += (int64_t)(nb >> 1) * (2 * w + 1) + (int64_t)(nb & 1) * (w + 1);
         }
         while (!stop && r < last_r) {     // r > w + 1 here
             ++r;
@@ -802,7 +945,8 @@ struct WarpPair16 {
             end_t = reach ? cold.mqe_t : cold.gt;
             end_q = reach ? qlen - 1 : cold.gq;
         }
-        if (lane == 0) {
+        group_sync();           // K > 1: every warp's last writes to cold are in
+        if (leader()) {
             agatha_result o;
             const int32_t mqe = cold.mqe;
             o.max = gmax; o.te = cold.gt; o.qe = cold.gq;
@@ -930,6 +1074,56 @@ warp16_align_kernel(const DevBatch *__restrict__ d_batch, int32_t use_fast, int3
             B.ovf_list[slot] = pair;
         }
     }
+    if (lane == 0) mark_step_end(B.counters);
+}
+
+// K warps of a block share one pair's band (K = 2: two pairs per block at a
+// time, K = 4: one): for the longest pairs, whose anti-diagonals then take
+// K times fewer steps of each warp (the paper's warps per task, Section 4.3,
+// here grown instead of split).  The group's first warp takes the next pair
+// from the queue and hands it to the others through shared memory.
+template <int C, int K, int MINB>
+__global__ void __launch_bounds__(WARP_BLOCK_THREADS, MINB)
+warp16k_align_kernel(const DevBatch *__restrict__ d_batch, int32_t use_fast, int32_t list) {
+    constexpr int G = WARP_BLOCK_THREADS / 32 / K;       // groups per block
+    __shared__ Cold16 cold[G];
+    __shared__ Xchg16 xch[G];
+    const DevBatch B = *d_batch;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int g = warp / K, wk = warp % K;
+    const int32_t bar = 1 + g;                           // named barrier of the group
+    const WorkList L = work_list(B, list);
+    for (;;) {
+        WarpPair16<C, (MINB < 4 && C <= 16) || MINB < 3, true, false, true, K> wp(cold[g], &xch[g], wk, bar);
+        if (wk == 0 && lane == 0) xch[g].pair = L.begin + atomicAdd(L.head, 1);
+        wp.group_sync();
+        const int32_t k = xch[g].pair;
+        wp.group_sync();
+        if (k >= L.end) break;
+        const int32_t pair = L.items ? L.items[k] : k;
+        if (!L.items && (!pair_valid(B, pair) || !warp_takes(B, pair))) continue;
+        if (!wp.run(B, pair, lane, use_fast != 0) && lane == 0 && wk == 0) {
+            const int32_t slot = atomicAdd(&B.counters[CTR_NOVF], 1);
+            B.ovf_list[slot] = pair;
+        }
+    }
+    if (lane == 0) mark_step_end(B.counters);
+}
+
+template <int C, int K, int MINB>
+cudaError_t launch_warp16k_c(const DevBatch *d_batch, int n_blocks, cudaStream_t s, int use_fast,
+                             int list) {
+    warp16k_align_kernel<C, K, MINB><<<n_blocks, WARP_BLOCK_THREADS, 0, s>>>(d_batch, use_fast, list);
+    return cudaGetLastError();
+}
+
+template <int C, int K, int MINB>
+int occupancy_warp16k_c() {
+    int nb = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, warp16k_align_kernel<C, K, MINB>,
+                                                      WARP_BLOCK_THREADS, 0) != cudaSuccess)
+        return 1;
+    return nb > 0 ? nb : 1;
 }
 
 template <int C, int MINB>

@@ -99,6 +99,9 @@ extern "C" int agatha_align_batch_noalloc(const agatha_batch *batch, const agath
     if (normalise_params(params, &p) != AGATHA_OK) return AGATHA_EINVAL;
     if (batch->n_pairs == 0) return AGATHA_OK;
     if (!out || !batch->q_len || !batch->t_len || !batch->q_off || !batch->t_off) return AGATHA_EINVAL;
+    // a stream the pairs may read must exist (an empty stream may be null)
+    if ((batch->q_words > 0 && !batch->q_packed) || (batch->t_words > 0 && !batch->t_packed))
+        return AGATHA_EINVAL;
 
     DeviceSetup *ds = nullptr;
     int rc = setup_current_device(&ds);

@@ -179,6 +179,30 @@ static cudaError_t launch_warp16(int C, int high, const DevBatch *d, int blocks,
     }
 }
 
+// 16-bit kernel with K warps per pair, for the band of the C16-slot kernel:
+// 2 warps of 8 or 12 slots per lane, 4 warps of 4 or 6.
+static cudaError_t launch_warp16k(int C16, int K, const DevBatch *d, int blocks, cudaStream_t s,
+                                  int fast, int list) {
+    switch (C16 * 8 + K) {
+        case 16 * 8 + 2: return launch_warp16k_c<8, 2, 4>(d, blocks, s, fast, list);
+        case 24 * 8 + 2: return launch_warp16k_c<12, 2, 4>(d, blocks, s, fast, list);
+        case 16 * 8 + 4: return launch_warp16k_c<4, 4, 6>(d, blocks, s, fast, list);
+        case 24 * 8 + 4: return launch_warp16k_c<6, 4, 4>(d, blocks, s, fast, list);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+// Resident blocks per SM of that kernel; 0 where none exists for C16.
+int warp16k_occupancy(int C16, int K) {
+    switch (C16 * 8 + K) {
+        case 16 * 8 + 2: return occupancy_warp16k_c<8, 2, 4>();
+        case 24 * 8 + 2: return occupancy_warp16k_c<12, 2, 4>();
+        case 16 * 8 + 4: return occupancy_warp16k_c<4, 4, 6>();
+        case 24 * 8 + 4: return occupancy_warp16k_c<6, 4, 4>();
+        default: return 0;
+    }
+}
+
 cudaError_t launch_overflow_int32(const Slot *sl, const LaunchPlan &lp, cudaStream_t s) {
     return launch_warp(lp.C, sl->d_desc, lp.warp_blocks, s, lp.fast, WARP_LIST_OVERFLOW);
 }
@@ -239,7 +263,11 @@ static cudaError_t enqueue_part(agatha_ctx *ctx, Slot *sl, const LaunchPlan &lp,
     if (lp.plain) return launch_plain_kernel(d, lp.plain_blocks, lp.plain_w, 0, s);
     bool any16 = false;
     if (!lp.split) {
-        if (lp.lane16) {
+        if (lp.lane16 && lp.groupk > 1) {
+            e = launch_warp16k(lp.C16, lp.groupk, d, lp.warp16k_blocks[lp.groupk == 4], s, lp.fast,
+                               WARP_LIST_MAIN);
+            any16 = true;
+        } else if (lp.lane16) {
             e = launch_warp16(lp.C16, lp.regs_high, d, lp.warp16_blocks[lp.regs_high], s, lp.fast,
                               WARP_LIST_MAIN);
             any16 = true;
@@ -257,6 +285,10 @@ static cudaError_t enqueue_part(agatha_ctx *ctx, Slot *sl, const LaunchPlan &lp,
             const int v = lp.cls_var[c];
             if (v == VAR_32) {
                 e = launch_warp(lp.C, d, lp.warp_blocks, sc, lp.fast, WARP_LIST_CLASS + c);
+            } else if (v == VAR_16_K2 || v == VAR_16_K4) {
+                const int K = variant_warps(v);
+                e = launch_warp16k(lp.C16, K, d, lp.warp16k_blocks[K == 4], sc, lp.fast, WARP_LIST_CLASS + c);
+                any16 = true;
             } else {
                 e = launch_warp16(lp.C16, v == VAR_16_HIGHREG, d, lp.warp16_blocks[v == VAR_16_HIGHREG],
                                   sc, lp.fast, WARP_LIST_CLASS + c);
@@ -415,10 +447,19 @@ int make_plan(agatha_ctx *ctx, const DevParams &p, const BatchShape &shape, uint
     lp->lane16 = !(flags & AGATHA_FORCE32) && lp->C16 > 0 && step_change_max(p) <= STEP16_MAX && !lp->wide_w;
     lp->regs_high = (flags & AGATHA_REGS_HIGH) ? 1 : 0;
     lp->split = 0;
+    lp->groupk = 1;
     if (lp->lane16) {
         lp->warp_w_max = 32 * lp->C16 - 1;
         lp->warp16_blocks[0] = ctx->n_sm * warp16_occupancy(lp->C16, 0);
         lp->warp16_blocks[1] = ctx->n_sm * warp16_occupancy(lp->C16, 1);
+        lp->warp16k_blocks[0] = ctx->n_sm * warp16k_occupancy(lp->C16, 2);
+        lp->warp16k_blocks[1] = ctx->n_sm * warp16k_occupancy(lp->C16, 4);
+        const int K = (flags & AGATHA_WARPS4) ? 4 : ((flags & AGATHA_WARPS2) ? 2 : 1);
+        if (K > 1) {
+            if (!lp->warp16k_blocks[K == 4])
+                return set_error(ctx, AGATHA_ENOTSUP, "%d warps per pair need a band of 256 to 767", K);
+            lp->groupk = K;
+        }
     }
     lp->plain_w = 0;
     lp->plain_blocks = 0;

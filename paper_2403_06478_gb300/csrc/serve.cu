@@ -207,10 +207,12 @@ struct ServeState {
     // statistics (under mu)
     int64_t requests_done = 0, pairs_done = 0, cells_done = 0, launches = 0;
     int64_t peak_bytes = 0;
-    int n_busy = 0;
+    int n_busy = 0, max_busy = 0;
     double busy_seconds = 0;
     Clock::time_point busy_since;
     std::vector<double> latencies_ms;
+    // device-clock span (ns) of every finished launch's kernels
+    std::vector<std::pair<uint64_t, uint64_t>> dev_spans;
 };
 
 namespace {
@@ -272,6 +274,12 @@ void reap(ServeState *S, ServeSlot *s) {
     int status = AGATHA_OK;
     if (s->failed) status = AGATHA_ECUDA;
     else if (s->slot.h_counters[CTR_ERR] != DEV_ERR_NONE) status = AGATHA_EDEVICE;
+    if (!s->failed) {
+        uint64_t t0 = 0, t1 = 0;
+        std::memcpy(&t0, s->slot.h_counters + CTR_T_BEGIN, sizeof(t0));
+        std::memcpy(&t1, s->slot.h_counters + CTR_T_END, sizeof(t1));
+        if (t0 > 0 && t1 >= t0) S->dev_spans.emplace_back(t0, t1);
+    }
     finish_requests(S, s, status);
     S->arena.release(s->block_off, s->block_bytes);
     s->block_off = -1;
@@ -447,6 +455,7 @@ void scheduler(ServeState *S) {
             s->failed = false;
             s->t_launch = Clock::now();
             if (S->n_busy++ == 0) S->busy_since = s->t_launch;
+            S->max_busy = std::max(S->max_busy, S->n_busy);
             S->launches += 1;
             S->peak_bytes = std::max(S->peak_bytes, S->arena.used());
             lk.unlock();
@@ -634,6 +643,25 @@ extern "C" int agatha_serve_stats_get(agatha_ctx *ctx, agatha_serve_stats *st) {
         st->p50_latency_ms = pct(0.50);
         st->p99_latency_ms = pct(0.99);
     }
+    st->max_launches_in_flight = S->max_busy;
+    // sweep over the launches' device spans: how many cover each instant
+    std::vector<std::pair<uint64_t, int>> ev;
+    ev.reserve(2 * S->dev_spans.size());
+    for (const auto &sp : S->dev_spans) {
+        ev.emplace_back(sp.first, +1);
+        ev.emplace_back(sp.second, -1);
+    }
+    std::sort(ev.begin(), ev.end());          // at equal times an end sorts before a start
+    int64_t cover = 0, most = 0;
+    uint64_t overlap_ns = 0, prev = 0;
+    for (const auto &x : ev) {
+        if (cover >= 2) overlap_ns += x.first - prev;
+        cover += x.second;
+        most = std::max(most, cover);
+        prev = x.first;
+    }
+    st->max_device_concurrency = most;
+    st->overlap_seconds = (double)overlap_ns * 1e-9;
     return AGATHA_OK;
 }
 

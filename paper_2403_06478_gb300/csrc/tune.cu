@@ -2,8 +2,10 @@
 //
 // The paper picks its slice width and subwarp size by sweeping them on its
 // datasets (Sections 5.5 and 5.7).  Here the knobs are those of the warp
-// kernels: 16-bit packed lanes or int32 lanes, and the register budget of
-// the 16-bit kernel (fewer resident warps, more registers each).  They are
+// kernels: 16-bit packed lanes or int32 lanes, the register budget of the
+// 16-bit kernel (fewer resident warps, more registers each), and how many
+// warps share one pair's band (1, 2 or 4: lanes per pair, for the classes of
+// long pairs, whose anti-diagonals then take fewer steps of each warp).  They are
 // chosen per length class, by measurement, the first time a host batch
 // arrives for a scoring and band width: the pairs of each class (up to 4096,
 // spread over the class) are aligned with every variant and the fastest one
@@ -80,7 +82,15 @@ LaunchPlan single_variant(LaunchPlan vp, int variant) {
     vp.split = 0;
     vp.lane16 = variant != VAR_32;
     vp.regs_high = variant == VAR_16_HIGHREG;
+    vp.groupk = variant_warps(variant);
     return vp;
+}
+
+// Whether this plan can run a variant (the 2- and 4-warp kernels exist for
+// the 16- and 24-slot bands only).
+bool variant_available(const LaunchPlan &lp, int v) {
+    const int K = variant_warps(v);
+    return K == 1 || lp.warp16k_blocks[K == 4] > 0;
 }
 
 // A sub-batch of at most `cap` of the given pairs, spread over them.
@@ -129,18 +139,21 @@ int tune_run(agatha_ctx *ctx, const agatha_batch *b, const DevParams &p, uint32_
     // 1. each length class on its own (up to kTuneMaxPairs of it): the
     //    fastest variant per class
     TuneChoice per;
-    bool wins[N_VARIANTS] = {true, false, false};
+    bool wins[N_VARIANTS] = {true, false, false, false, false};
     for (int c = 0; c < N_CLASSES; ++c) {
         per.var[c] = VAR_16;
         if (members[c].empty()) continue;
         SubBatch sb(b, members[c], kTuneMaxPairs);
         float t[N_VARIANTS];
         for (int v = 0; v < N_VARIANTS; ++v) {
+            t[v] = 0.f;
+            // warps sharing a pair only for the classes of long pairs
+            if (!variant_available(lp, v) || (variant_warps(v) > 1 && c > 1)) continue;
             const int rc = time_plan(ctx, sb.b, p, flags, s, single_variant(lp, v), res, &t[v]);
             if (rc) return rc;
         }
         for (int v = 1; v < N_VARIANTS; ++v)
-            if (t[v] < kMargin * t[per.var[c]]) per.var[c] = (int8_t)v;
+            if (t[v] > 0.f && t[v] < kMargin * t[per.var[c]]) per.var[c] = (int8_t)v;
         wins[per.var[c]] = true;
     }
     choice->split = 0;
@@ -154,7 +167,7 @@ int tune_run(agatha_ctx *ctx, const agatha_batch *b, const DevParams &p, uint32_
     float best = 0.f;
     int best_v = VAR_16;
     for (int v = 0; v < N_VARIANTS; ++v) {
-        if (!wins[v]) continue;
+        if (!wins[v] || variant_warps(v) > 1) continue;    // the long classes' choice, not the batch's
         float t = 0.f;
         const int rc = time_plan(ctx, whole.b, p, flags, s, single_variant(lp, v), res, &t);
         if (rc) return rc;
@@ -205,7 +218,8 @@ void tune_load(agatha_ctx *ctx) {
 
 int tune_apply(agatha_ctx *ctx, const agatha_batch *batch, const DevParams &p, uint32_t flags,
                cudaStream_t s, LaunchPlan *lp) {
-    const uint32_t off = AGATHA_NO_TUNE | AGATHA_PLAIN | AGATHA_FORCE32 | AGATHA_NO_SORT | AGATHA_REGS_HIGH;
+    const uint32_t off = AGATHA_NO_TUNE | AGATHA_PLAIN | AGATHA_FORCE32 | AGATHA_NO_SORT | AGATHA_REGS_HIGH |
+                         AGATHA_WARPS2 | AGATHA_WARPS4;
     if (!ctx->autotune || (flags & off) || lp->plain || !lp->lane16 || !lp->sort) return AGATHA_OK;
     const std::string key = tune_key(ctx, p, lp->C16);
     TuneChoice choice;
@@ -227,10 +241,14 @@ int tune_apply(agatha_ctx *ctx, const agatha_batch *batch, const DevParams &p, u
     }
     if (!choice.split) {                        // one launch of one variant
         const int v = choice.var[0];
+        if (!variant_available(*lp, v)) return AGATHA_OK;
         lp->lane16 = v != VAR_32;
         lp->regs_high = v == VAR_16_HIGHREG;
+        lp->groupk = variant_warps(v);
         return AGATHA_OK;
     }
+    for (int c = 0; c < N_CLASSES; ++c)
+        if (!variant_available(*lp, choice.var[c])) return AGATHA_OK;
     lp->split = 1;
     for (int c = 0; c < N_CLASSES; ++c) lp->cls_var[c] = choice.var[c];
     return AGATHA_OK;

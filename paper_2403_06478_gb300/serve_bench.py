@@ -11,6 +11,12 @@ one is done, so tail figures are, if anything, pessimistic).  The library's
 own submit-to-completion percentiles are reported beside them.
 
     python -m paper_2403_06478_gb300.serve_bench [--rates 10,100,1000] [--budget-gb 16]
+        [--tune-cache FILE]
+
+Each line also carries the overlap figures of the server (launches in
+flight at once, and from the device's global timer the most launches whose
+kernels ran at one instant and the device time with two or more), the tuned
+plan the merged launches used, and the GPU clocks sampled during the point.
 """
 from __future__ import annotations
 
@@ -24,6 +30,7 @@ import numpy as np
 from . import agatha as A
 from . import build as B
 from . import workload as W
+from .clocks import ClockSampler
 
 
 def _point(ctx, pool_pb, pool, rate, args, rng):
@@ -49,6 +56,8 @@ def _point(ctx, pool_pb, pool, rate, args, rng):
 
     th = threading.Thread(target=waiter)
     th.start()
+    sampler = ClockSampler(args.device)
+    sampler.start()
     t0 = time.perf_counter()
     for i, r in enumerate(reqs):
         delay = t0 + r.arrival_s - time.perf_counter()
@@ -58,6 +67,7 @@ def _point(ctx, pool_pb, pool, rate, args, rng):
         submitted.release()
     th.join()
     t_end = max(done_at)
+    clocks = sampler.stop()
     st = srv.stats()
     srv.stop(drain=True)
     lat = np.array([done_at[i] - (t0 + reqs[i].arrival_s) for i in range(n_req)]) * 1e3
@@ -71,6 +81,10 @@ def _point(ctx, pool_pb, pool, rate, args, rng):
         "lib_p50_ms": st["p50_latency_ms"], "lib_p99_ms": st["p99_latency_ms"],
         "launches": st["launches"], "busy_s": st["busy_seconds"], "wall_s": wall,
         "peak_bytes_in_flight": st["peak_bytes_in_flight"],
+        "max_launches_in_flight": st["max_launches_in_flight"],
+        "max_device_concurrency": st["max_device_concurrency"],
+        "device_overlap_s": st["overlap_seconds"],
+        "clocks": clocks,
     }
 
 
@@ -85,11 +99,13 @@ def main(argv=None):
     ap.add_argument("--max-batch-pairs", type=int, default=8192)
     ap.add_argument("--linger-us", type=int, default=0)
     ap.add_argument("--device", type=int, default=0)
+    ap.add_argument("--tune-cache", default=None,
+                    help="autotuner cache file (the benchmark's, to serve with the same plan)")
     args = ap.parse_args(argv)
     B.build()
     pool = W.make_config("ont")
     pool_pb = A.pack_batch(pool)
-    ctx = A.Context(args.device, autotune=True)
+    ctx = A.Context(args.device, autotune=True, tune_cache_path=args.tune_cache)
     # the autotuner measures its plan on one host batch of the scoring; the
     # server's merged launches then use it
     ctx.align_host(pool_pb, pool.scoring)

@@ -105,3 +105,17 @@ def _band_cells_ref(tlen, qlen, w):
                                       (100, 60, 20), (1, 1, 1)])
 def test_band_cells(tl, ql, w):
     assert A.agatha_band_cells(tl, ql, w) == _band_cells_ref(tl, ql, w)
+
+
+def test_noalloc_rejects_null_streams_on_the_host():
+    # host-side checks only: these calls return before any CUDA call, so they
+    # run without a GPU (the pointer values are never dereferenced)
+    for qp, tp in ((None, 16), (16, None)):
+        with pytest.raises(A.AgathaError) as e:
+            A.agatha_align_batch_noalloc(qp, tp, 8, 8, 8, 8, 8, W.ONT_SCORING, n_pairs=1,
+                                         words=(4, 4))
+        assert e.value.code == A.AGATHA_EINVAL
+    with pytest.raises(A.AgathaError) as e:
+        A.agatha_align_batch_noalloc(16, 16, 8, 8, 8, 8, 8, W.ONT_SCORING,
+                                     n_pairs=A.AGATHA_NOALLOC_MAX_PAIRS + 1, words=(4, 4))
+    assert e.value.code == A.AGATHA_EINVAL

@@ -255,3 +255,80 @@ def test_device_pointers_and_device_side_check(ctx):
         ctx.align_device(dev["q_packed"], dev["t_packed"], dev["q_off"], bad_off, dev["q_len"],
                          dev["t_len"], out, batch.scoring)
     assert e.value.code == A.AGATHA_EINVAL
+
+
+@pytest.mark.parametrize("f", [0.01, 0.1, 0.5])
+def test_long_ratio_mix_matches_oracle(ctx, f):
+    # the paper's load-balancing mix (Section 5.6): a fraction f of 4096 bp
+    # pairs among 128 bp ones; every pair against the oracle on the
+    # longest-first queue, the same queue in input order and the plain kernel
+    batch = W.make_long_ratio(f, n_pairs=2000)
+    assert int((batch.q_len == 4096).sum()) == round(f * 2000)
+    ref = O.align_batch(batch)
+    for path in ("batched", "no_sort", "plain"):
+        got = A.agatha_align_batch(ctx, batch, flags=PATHS[path])
+        _assert_same(got, ref, batch, f"long_ratio {f}/{path}")
+
+
+# 2 and 4 warps sharing each pair's band (bands of 256..767 slots)
+WARPS_SCORINGS = [
+    W.Scoring(2, 4, 4, 2, 24, 1, 300, 400, 0),
+    W.Scoring(2, 4, 4, 2, 24, 1, 511, 400, 0),      # 16-slot frame exactly full
+    W.Scoring(1, 4, 6, 2, 26, 1, 600, 200, 5),      # HiFi scoring, end bonus, 24-slot frame
+    W.Scoring(2, 4, 4, 2, 24, 1, 767, 30, 0),       # 24-slot frame full, frequent Z-drop
+    W.Scoring(2, 3, 2, 3, 5, 1, 256, 0, 0),         # zdrop 0
+    W.Scoring(1, 20, 4, 30, 4, 30, 400, -1, 0),     # steep single-piece gaps, no Z-drop
+]
+
+
+@pytest.mark.parametrize("si", range(len(WARPS_SCORINGS)))
+@pytest.mark.parametrize("warps", ["warps2", "warps4"])
+def test_warps_per_pair_match_oracle(ctx, si, warps):
+    scoring = WARPS_SCORINGS[si]
+    flags = A.AGATHA_WARPS2 if warps == "warps2" else A.AGATHA_WARPS4
+    batch = _adversarial_batch(np.random.default_rng(300 + si), scoring)
+    ref = O.align_batch(batch)
+    _assert_same(A.agatha_align_batch(ctx, batch, flags=flags), ref, batch, f"{warps}[{si}]")
+    _assert_same(A.agatha_align_batch(ctx, batch, flags=flags | A.AGATHA_EDGE_PATH_ONLY), ref, batch,
+                 f"{warps}[{si}]/edge")
+
+
+@pytest.mark.parametrize("name", ["ont", "skewed"])
+@pytest.mark.parametrize("warps", ["warps2", "warps4"])
+def test_warps_per_pair_on_workloads(ctx, name, warps):
+    # the longest pairs of the workload (the ones this variant is for) and a
+    # sample of the rest, against the oracle
+    flags = A.AGATHA_WARPS2 if warps == "warps2" else A.AGATHA_WARPS4
+    batch = W.make_config(name, n_pairs=4000)
+    L = np.maximum(batch.q_len, batch.t_len).astype(np.int64)
+    idx = np.unique(np.concatenate([np.argsort(-L)[:24],
+                                    np.random.default_rng(41).choice(batch.n_pairs, 200, replace=False)]))
+    sub = batch.subset(idx)
+    got = A.agatha_align_batch(ctx, sub, flags=flags)
+    assert got["lane16"].mean() > 0.99
+    _assert_same(got, O.align_batch(sub), sub, f"{name}/{warps}")
+    # and the whole 4,000 pairs equal the one-warp kernel's results
+    assert A.results_equal(A.agatha_align_batch(ctx, batch, flags=flags),
+                           A.agatha_align_batch(ctx, batch)).size == 0
+
+
+def test_warps_per_pair_hand_back_overflow(ctx):
+    # the 16-bit overflow case with 2 and 4 warps: every warp of the group
+    # must agree to hand the pair to the int32 kernel
+    rng = np.random.default_rng(17)
+    scoring = W.Scoring(64, 64, 1, 63, 1, 63, 511, -1, 0)
+    xs = [rng.integers(0, 4, 2500 + 100 * k).astype(np.uint8) for k in range(4)]
+    ys = [rng.integers(0, 4, 250).astype(np.uint8) for _ in range(4)]
+    batch = W.from_pairs(xs + ys, [x.copy() for x in xs + ys], scoring)
+    ref = O.align_batch(batch)
+    for flags in (A.AGATHA_WARPS2, A.AGATHA_WARPS4):
+        got = A.agatha_align_batch(ctx, batch, flags=flags)
+        _assert_same(got, ref, batch, f"overflow/{flags}")
+        assert (got["lane16"][:4] == 0).all() and (got["lane16"][4:] == 1).all()
+
+
+def test_warps_per_pair_rejects_other_bands(ctx):
+    batch = W.make_config("small", n_pairs=8)          # w = 100: 4-slot frame
+    with pytest.raises(A.AgathaError) as e:
+        A.agatha_align_batch(ctx, batch, flags=A.AGATHA_WARPS2)
+    assert e.value.code == A.AGATHA_ENOTSUP

@@ -159,3 +159,23 @@ def test_serving_uses_the_tuned_plan(tmp_path, ctx, pools):
     assert st["requests_done"] == len(reqs)
     for b, g in zip(reqs, got):
         assert A.results_equal(g, A.agatha_align_batch(ctx, b)).size == 0
+
+
+def test_burst_runs_launches_concurrently_on_the_device(ctx, pools):
+    # a burst of ONT-like requests, one request per launch: the next launch's
+    # kernels start while the previous one's longest pairs still run, which
+    # the device's global timer shows (first block of a launch's first kernel
+    # before the last warp of the running launch finished)
+    rng = np.random.default_rng(31)
+    pool = pools["ont"]
+    reqs = [pool.subset(rng.choice(pool.n_pairs, 64, replace=False)) for _ in range(24)]
+    got, st = _serve_all(ctx, reqs, max_inflight=3, max_batch_pairs=64)
+    assert st["requests_done"] == len(reqs)
+    assert st["launches"] == len(reqs)
+    assert st["max_launches_in_flight"] >= 2
+    assert st["max_device_concurrency"] >= 2
+    assert st["overlap_seconds"] > 0
+    for i, (b, g) in enumerate(zip(reqs, got)):
+        assert A.results_equal(g, A.agatha_align_batch(ctx, b)).size == 0, f"request {i}"
+    for i in (0, 11):
+        assert A.results_equal(got[i], O.align_batch(reqs[i]), O.COMPARE_FIELDS).size == 0

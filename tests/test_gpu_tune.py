@@ -53,7 +53,8 @@ def test_tuning_fills_cache_and_keeps_results(tmp_path, batch, reference):
 
 
 @pytest.mark.parametrize("variants", [(2, 1, 0, 2), (1, 2, 1, 0), (0, 0, 2, 1), (2, 2, 2, 2),
-                                      (0, 0, 0, 0)])
+                                      (0, 0, 0, 0), (3, 3, 1, 1), (4, 3, 0, 1), (4, 4, 4, 4),
+                                      (3, 1, 2, 3)])
 def test_every_class_variant_is_exact(tmp_path, batch, reference, variants):
     path = tmp_path / "tune.txt"
     path.write_text(_key(batch.scoring, 16) + " " + " ".join(map(str, variants)) + " 1\n")
@@ -72,7 +73,7 @@ def test_every_class_variant_is_exact(tmp_path, batch, reference, variants):
         assert A.results_equal(out.cpu().numpy().view(A.RESULT_DTYPE), reference).size == 0
 
 
-@pytest.mark.parametrize("variant", [1, 2])
+@pytest.mark.parametrize("variant", [1, 2, 3, 4])
 def test_single_launch_of_another_variant_is_exact(tmp_path, batch, reference, variant):
     path = tmp_path / "tune.txt"
     path.write_text(_key(batch.scoring, 16) + f" {variant} {variant} {variant} {variant} 0\n")

@@ -56,3 +56,19 @@ def test_short_read_workload():
     assert abs(float(np.mean(b.t_len.astype(np.int64) - b.q_len))) < 1
     again = W.make_config("short", n_pairs=2000)
     assert np.array_equal(b.t_codes, again.t_codes)
+
+
+def test_full_batch_oracle_digests_match_the_generator():
+    # the stored oracle digests of the full-size workloads (written by
+    # tests/golden/full_batch_digests.py from the oracle alone) were taken on
+    # exactly the inputs this generator draws; the GPU test of every pair
+    # relies on that, and falls back to a live oracle run where it fails
+    from golden import full_batch_digests as G
+    recs = G.read_golden()
+    assert sorted(recs) == sorted(G.CONFIGS)
+    for name, rec in recs.items():
+        batch = W.make_config(name)
+        assert rec["n_pairs"] == batch.n_pairs
+        assert len(rec["chunks"]) == -(-batch.n_pairs // rec["chunk"])
+        assert G.input_digest(batch) == rec["input"], name
+        assert 0 < rec["zdropped"] < batch.n_pairs

@@ -58,6 +58,52 @@ def test_noalloc_matches_regular_entry_point_on_two_calls_in_a_row():
         assert int(got["cells"].sum()) == int(ref["cells"].sum()) > 0
 
 
+@pytest.mark.parametrize("w", [750, 1000, -1, 1500])
+def test_noalloc_wide_bands_match_regular_entry_point(w):
+    # w = 750 and 1000 run the 24- and 32-slot warp kernels; w = -1 (unbanded)
+    # and w = 1500 send every pair through the plain block kernel's list in the
+    # scratch array, whose counter must restart at zero on every call
+    torch = pytest.importorskip("torch")
+    B.build()
+    batch = W.make_config("ont", n_pairs=600).with_scoring(w=w)
+    # unbanded and w = 1500 pairs go to the plain kernel, whose band (shared
+    # memory) holds about 4,600 slots: keep the tables below that
+    lens = np.maximum(batch.q_len, batch.t_len)
+    batch = batch.subset(np.flatnonzero(lens <= 3000)[:200])
+    pb, dev = _device_batch(torch, batch)
+    with A.Context(0) as ctx:
+        ref = _regular(ctx, dev, batch.scoring, pb.n_pairs, torch)
+    for _ in range(2):
+        got = _noalloc(dev, batch.scoring, batch.n_pairs, torch)
+        bad = A.results_equal(got, ref)
+        assert bad.size == 0, (w, bad[:10])
+
+
+def test_noalloc_reports_a_pair_outside_its_stream():
+    torch = pytest.importorskip("torch")
+    B.build()
+    batch = W.make_config("small", n_pairs=64)
+    pb, dev = _device_batch(torch, batch)
+    with A.Context(0) as ctx:
+        ref = _regular(ctx, dev, batch.scoring, pb.n_pairs, torch)
+    bad_off = dev["t_off"].clone()
+    bad_off[5] = int(pb.t_packed.shape[0]) * 16 + 100      # past the end of the target stream
+    out = torch.full((pb.n_pairs * 48,), 0xAB, dtype=torch.uint8, device="cuda")
+    with pytest.raises(A.AgathaError) as e:
+        A.agatha_align_batch_noalloc(dev["q_packed"], dev["t_packed"], dev["q_off"], bad_off,
+                                     dev["q_len"], dev["t_len"], out, batch.scoring)
+    assert e.value.code == A.AGATHA_EINVAL
+    got = out.cpu().numpy().view(A.RESULT_DTYPE).copy()
+    r = got[5]
+    assert (r["max"], r["qe"], r["te"], r["gscore"], r["cells"], r["zdropped"]) == (
+        0, -1, -1, A.NEG_INF, 0, 0)
+    keep = np.arange(pb.n_pairs) != 5
+    assert A.results_equal(got[keep], ref[keep]).size == 0
+    # the next call on good input is unaffected by the error the last one left
+    got = _noalloc(dev, batch.scoring, batch.n_pairs, torch)
+    assert A.results_equal(got, ref).size == 0
+
+
 def test_noalloc_rejects_batches_over_its_limit():
     torch = pytest.importorskip("torch")
     B.build()
