@@ -21,6 +21,9 @@
  *   - After the score path, the traceback (CIGAR) of one extension: the
  *     edit operations of a best path to its end cell, under a stated tie
  *     rule (orc_traceback_pair, at the end of this file).
+ *   - The BWA-MEM variant of the extension (Section 5.9): local extension
+ *     from an initial score with BWA-MEM's row-by-row termination
+ *     (orc_align_pair_local).
  * Readings where the paper is silent (boundary, tie-breaks, outputs) follow the
  * minimap2 extension convention and are listed in the design notes.
  *
@@ -190,6 +193,123 @@ void orc_normalise(orc_params *p)
 }
 
 /* ----------------------------------------------------------------------- */
+/*
+ * Local extension from an initial score: the BWA-MEM variant of the
+ * extension (the paper applies its kernel to BWA-MEM's guided alignment,
+ * Section 5.9).  This implementation's reading of BWA-MEM's published
+ * extension rules (the BWA-MEM paper, seed extension and clipping), also
+ * listed in the design notes:
+ *   - the extension continues an alignment whose score so far is h0 > 0: the
+ *     origin (-1,-1) holds h0, the virtual row and column h0 - gap(l);
+ *   - a path is kept only while its score stays positive: every cell state
+ *     (H, E, F, E2, F2) holds the best score of a path ending there whose
+ *     score was positive after every step, and 0 when there is none; a
+ *     diagonal step out of an empty cell (H = 0) stays empty;
+ *   - the table is processed one query position (row q) at a time; the best
+ *     cell of a row (lowest t on ties) becomes the best so far when strictly
+ *     higher, otherwise the Z-drop test stops the extension when
+ *     best - row_best > zdrop + |(q - qe) - (t_row - te)| e2 (always tested,
+ *     zdrop < 0: off); a row with no positive cell ends the extension;
+ *   - mqe/mqe_t: the best cell of the last query row, mte/mte_q the best
+ *     positive cell of the last target base, gscore the cell (tlen-1,
+ *     qlen-1), each only from the rows processed; reach_end (the end-to-end
+ *     choice of BWA-MEM's clipping rule): no early stop and mqe + end_bonus
+ *     beats the best local score;
+ *   - zdropped is set by either kind of early stop; cells counts the band
+ *     cells of the rows processed, the stopping one included.
+ * Nothing beats h0: max = h0, qe = te = -1.
+ */
+static int64_t pos64(int64_t x) { return x > 0 ? x : 0; }
+
+void orc_align_pair_local(const uint8_t *T, int32_t tlen, const uint8_t *Q, int32_t qlen,
+                          const orc_params *p_in, int32_t h0, orc_result *out)
+{
+    orc_params p = *p_in;
+    memset(out, 0, sizeof(*out));
+    out->max = h0; out->qe = -1; out->te = -1;
+    out->gscore = ORC_OUT_NEG_INF; out->mqe = ORC_OUT_NEG_INF; out->mte = ORC_OUT_NEG_INF;
+    out->mqe_t = -1; out->mte_q = -1;
+    if (tlen <= 0 || qlen <= 0) return;
+
+    int64_t w = p.w;
+    if (w < 0 || w > (int64_t)(tlen > qlen ? tlen : qlen)) w = tlen > qlen ? tlen : qlen;
+
+    /* prev[t]: row q-1, cur[t]: row q */
+    cell_state *prev = (cell_state *)malloc(sizeof(cell_state) * (size_t)tlen);
+    cell_state *cur = (cell_state *)malloc(sizeof(cell_state) * (size_t)tlen);
+    if (!prev || !cur) { free(prev); free(cur); out->zdropped = 255; return; }
+
+    int64_t gmax = h0, gmax_t = -1, gmax_q = -1;
+    int64_t mqe = ORC_MINUS_INF, mqe_t = -1, mte = ORC_MINUS_INF, mte_q = -1;
+    int64_t gscore = ORC_MINUS_INF;
+    int64_t cells = 0;
+    int zdropped = 0;
+
+    for (int64_t q = 0; q < qlen; ++q) {
+        int64_t lo = q - w > 0 ? q - w : 0;
+        int64_t hi = q + w < tlen - 1 ? q + w : tlen - 1;
+        if (lo > hi) { zdropped = 1; break; }           /* the band left the table */
+        int64_t row_best = 0, row_t = -1;
+        for (int64_t t = lo; t <= hi; ++t) {
+            /* diagonal predecessor H(t-1, q-1) */
+            int64_t Hdiag;
+            if (t == 0 && q == 0) Hdiag = h0;
+            else if (t == 0) Hdiag = pos64(h0 - gap_cost(&p, q));        /* H(-1, q-1) */
+            else if (q == 0) Hdiag = pos64(h0 - gap_cost(&p, t));        /* H(t-1, -1) */
+            else Hdiag = in_band(t - 1, q - 1, tlen, qlen, w) ? prev[t - 1].H : 0;
+            /* (t-1, q), the previous cell of this row: E and E2 */
+            int64_t Hup, Eup, E2up;
+            if (t == 0) { Hup = pos64(h0 - gap_cost(&p, q + 1)); Eup = 0; E2up = 0; }
+            else if (t - 1 >= lo) { Hup = cur[t - 1].H; Eup = cur[t - 1].E; E2up = cur[t - 1].E2; }
+            else { Hup = 0; Eup = 0; E2up = 0; }
+            /* (t, q-1), the previous row: F and F2 */
+            int64_t Hleft, Fleft, F2left;
+            if (q == 0) { Hleft = pos64(h0 - gap_cost(&p, t + 1)); Fleft = 0; F2left = 0; }
+            else if (in_band(t, q - 1, tlen, qlen, w)) { Hleft = prev[t].H; Fleft = prev[t].F; F2left = prev[t].F2; }
+            else { Hleft = 0; Fleft = 0; F2left = 0; }
+
+            int64_t E = pos64(imax64(Hup - p.q - p.e, Eup - p.e));
+            int64_t E2 = pos64(imax64(Hup - p.q2 - p.e2, E2up - p.e2));
+            int64_t F = pos64(imax64(Hleft - p.q - p.e, Fleft - p.e));
+            int64_t F2 = pos64(imax64(Hleft - p.q2 - p.e2, F2left - p.e2));
+            int64_t s = (T[t] == Q[q]) ? p.a : -(int64_t)p.b;
+            int64_t H = Hdiag > 0 ? pos64(Hdiag + s) : 0;
+            H = imax64(H, E); H = imax64(H, F); H = imax64(H, E2); H = imax64(H, F2);
+            cur[t].H = H; cur[t].E = E; cur[t].F = F; cur[t].E2 = E2; cur[t].F2 = F2;
+            if (H > row_best) { row_best = H; row_t = t; }  /* positive only, lowest t */
+        }
+        cells += hi - lo + 1;
+
+        /* the last target base and the last query row */
+        if (hi == tlen - 1 && cur[tlen - 1].H > 0 && cur[tlen - 1].H > mte) {
+            mte = cur[tlen - 1].H; mte_q = q;
+        }
+        if (q == qlen - 1 && row_best > 0) { mqe = row_best; mqe_t = row_t; }
+        if (row_best == 0) { zdropped = 1; break; }      /* no live cell left */
+        if (row_best > gmax) {
+            gmax = row_best; gmax_t = row_t; gmax_q = q;
+        } else if (p.zdrop >= 0) {
+            int64_t dq = q - gmax_q, dt = row_t - gmax_t;
+            int64_t l = dq > dt ? dq - dt : dt - dq;
+            if (gmax - row_best > (int64_t)p.zdrop + l * p.e2) { zdropped = 1; break; }
+        }
+        if (q == qlen - 1 && hi == tlen - 1 && cur[tlen - 1].H > 0) gscore = cur[tlen - 1].H;
+
+        cell_state *tmp = prev; prev = cur; cur = tmp;
+    }
+
+    out->max = (int32_t)gmax; out->te = (int32_t)gmax_t; out->qe = (int32_t)gmax_q;
+    out->gscore = gscore == ORC_MINUS_INF ? ORC_OUT_NEG_INF : (int32_t)gscore;
+    out->mqe = mqe == ORC_MINUS_INF ? ORC_OUT_NEG_INF : (int32_t)mqe;
+    out->mte = mte == ORC_MINUS_INF ? ORC_OUT_NEG_INF : (int32_t)mte;
+    out->mqe_t = (int32_t)mqe_t; out->mte_q = (int32_t)mte_q;
+    out->cells = cells;
+    out->zdropped = (uint8_t)zdropped;
+    out->reach_end = (uint8_t)(!zdropped && mqe != ORC_MINUS_INF && mqe + p.end_bonus > gmax);
+    free(prev); free(cur);
+}
+
+/* ----------------------------------------------------------------------- */
 /* Batch driver: pairs spread over threads, longest first, for timing only. */
 
 typedef struct {
@@ -199,6 +319,7 @@ typedef struct {
     const int64_t *order;
     int64_t n;
     orc_params p;
+    const int32_t *h0;        /* non-null: the local extension with these initial scores */
     orc_result *out;
     int64_t next;
     pthread_mutex_t lock;
@@ -214,23 +335,28 @@ static void *orc_worker(void *arg)
         pthread_mutex_unlock(&job->lock);
         if (k >= job->n) break;
         int64_t i = job->order ? job->order[k] : k;
-        orc_align_pair(job->t_codes + job->t_off[i], job->t_len[i],
-                       job->q_codes + job->q_off[i], job->q_len[i], &job->p, &job->out[i]);
+        if (job->h0)
+            orc_align_pair_local(job->t_codes + job->t_off[i], job->t_len[i],
+                                 job->q_codes + job->q_off[i], job->q_len[i], &job->p, job->h0[i],
+                                 &job->out[i]);
+        else
+            orc_align_pair(job->t_codes + job->t_off[i], job->t_len[i],
+                           job->q_codes + job->q_off[i], job->q_len[i], &job->p, &job->out[i]);
     }
     return NULL;
 }
 
-/* Align n pairs with n_threads threads; order (may be NULL) is the schedule. */
-int orc_align_batch(const uint8_t *q_codes, const uint8_t *t_codes,
-                    const int64_t *q_off, const int64_t *t_off,
-                    const int32_t *q_len, const int32_t *t_len,
-                    const int64_t *order, int64_t n, const orc_params *p,
-                    orc_result *out, int n_threads)
+static int orc_run_batch(const uint8_t *q_codes, const uint8_t *t_codes,
+                         const int64_t *q_off, const int64_t *t_off,
+                         const int32_t *q_len, const int32_t *t_len,
+                         const int64_t *order, int64_t n, const orc_params *p,
+                         const int32_t *h0, orc_result *out, int n_threads)
 {
     orc_job job;
     job.q_codes = q_codes; job.t_codes = t_codes; job.q_off = q_off; job.t_off = t_off;
     job.q_len = q_len; job.t_len = t_len; job.order = order; job.n = n;
     job.p = *p; orc_normalise(&job.p);
+    job.h0 = h0;
     job.out = out; job.next = 0;
     pthread_mutex_init(&job.lock, NULL);
     if (n_threads < 1) n_threads = 1;
@@ -244,6 +370,28 @@ int orc_align_batch(const uint8_t *q_codes, const uint8_t *t_codes,
     free(th);
     pthread_mutex_destroy(&job.lock);
     return 0;
+}
+
+/* Align n pairs with n_threads threads; order (may be NULL) is the schedule. */
+int orc_align_batch(const uint8_t *q_codes, const uint8_t *t_codes,
+                    const int64_t *q_off, const int64_t *t_off,
+                    const int32_t *q_len, const int32_t *t_len,
+                    const int64_t *order, int64_t n, const orc_params *p,
+                    orc_result *out, int n_threads)
+{
+    return orc_run_batch(q_codes, t_codes, q_off, t_off, q_len, t_len, order, n, p, NULL, out,
+                         n_threads);
+}
+
+/* The same for the local extension, h0[i] the initial score of pair i. */
+int orc_align_batch_local(const uint8_t *q_codes, const uint8_t *t_codes,
+                          const int64_t *q_off, const int64_t *t_off,
+                          const int32_t *q_len, const int32_t *t_len,
+                          const int64_t *order, int64_t n, const orc_params *p,
+                          const int32_t *h0, orc_result *out, int n_threads)
+{
+    return orc_run_batch(q_codes, t_codes, q_off, t_off, q_len, t_len, order, n, p, h0, out,
+                         n_threads);
 }
 
 int orc_result_size(void) { return (int)sizeof(orc_result); }

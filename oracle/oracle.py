@@ -69,6 +69,13 @@ def _load():
         lib.orc_align_batch.restype = ctypes.c_int
         lib.orc_align_batch.argtypes = [ctypes.c_void_p] * 7 + [
             ctypes.c_int64, ctypes.POINTER(_Params), ctypes.c_void_p, ctypes.c_int]
+        lib.orc_align_pair_local.restype = None
+        lib.orc_align_pair_local.argtypes = [ctypes.c_void_p, ctypes.c_int32, ctypes.c_void_p,
+                                             ctypes.c_int32, ctypes.POINTER(_Params), ctypes.c_int32,
+                                             ctypes.c_void_p]
+        lib.orc_align_batch_local.restype = ctypes.c_int
+        lib.orc_align_batch_local.argtypes = [ctypes.c_void_p] * 7 + [
+            ctypes.c_int64, ctypes.POINTER(_Params), ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int]
         lib.orc_result_size.restype = ctypes.c_int
         lib.orc_traceback_pair.restype = ctypes.c_int64
         lib.orc_traceback_pair.argtypes = [ctypes.c_void_p, ctypes.c_int32, ctypes.c_void_p,
@@ -98,9 +105,26 @@ def align_pair(target: np.ndarray, query: np.ndarray, scoring) -> np.void:
     return out[0]
 
 
+def align_pair_local(target: np.ndarray, query: np.ndarray, scoring, h0: int) -> np.void:
+    """Local extension of one pair from the initial score h0 (the BWA-MEM
+    variant); parameters are normalised first."""
+    lib = _load()
+    t = np.ascontiguousarray(target, dtype=np.uint8)
+    q = np.ascontiguousarray(query, dtype=np.uint8)
+    p = _params(scoring)
+    lib.orc_normalise(ctypes.byref(p))
+    out = np.zeros(1, dtype=RESULT_DTYPE)
+    lib.orc_align_pair_local(t.ctypes.data if len(t) else None, len(t),
+                             q.ctypes.data if len(q) else None, len(q), ctypes.byref(p), int(h0),
+                             out.ctypes.data)
+    return out[0]
+
+
 def align_batch(batch, idx: Optional[np.ndarray] = None, threads: Optional[int] = None,
-                longest_first: bool = True) -> np.ndarray:
-    """Align every pair of ``batch`` (or the pairs ``idx``) on host threads."""
+                longest_first: bool = True, h0: Optional[np.ndarray] = None) -> np.ndarray:
+    """Align every pair of ``batch`` (or the pairs ``idx``) on host threads;
+    with ``h0`` (one initial score per pair of the batch) the local extension
+    (the BWA-MEM variant) instead."""
     lib = _load()
     if idx is not None:
         idx = np.asarray(idx, dtype=np.int64)
@@ -130,10 +154,18 @@ def align_batch(batch, idx: Optional[np.ndarray] = None, threads: Optional[int] 
         tc = np.zeros(1, np.uint8)
     p = _params(batch.scoring)
     nt = threads if threads is not None else (os.cpu_count() or 1)
-    rc = lib.orc_align_batch(qc.ctypes.data, tc.ctypes.data, q_off.ctypes.data,
-                             t_off.ctypes.data, q_len.ctypes.data, t_len.ctypes.data,
-                             order.ctypes.data if order is not None else None,
-                             n, ctypes.byref(p), out.ctypes.data, int(nt))
+    if h0 is not None:
+        h = np.asarray(h0, dtype=np.int32)
+        h = np.ascontiguousarray(h[idx] if idx is not None else h)
+        rc = lib.orc_align_batch_local(qc.ctypes.data, tc.ctypes.data, q_off.ctypes.data,
+                                       t_off.ctypes.data, q_len.ctypes.data, t_len.ctypes.data,
+                                       order.ctypes.data if order is not None else None,
+                                       n, ctypes.byref(p), h.ctypes.data, out.ctypes.data, int(nt))
+    else:
+        rc = lib.orc_align_batch(qc.ctypes.data, tc.ctypes.data, q_off.ctypes.data,
+                                 t_off.ctypes.data, q_len.ctypes.data, t_len.ctypes.data,
+                                 order.ctypes.data if order is not None else None,
+                                 n, ctypes.byref(p), out.ctypes.data, int(nt))
     if rc != 0:
         raise RuntimeError("oracle batch failed")
     return out

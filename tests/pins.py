@@ -255,3 +255,100 @@ def cigar_score(ops, T, Q, p: Dict, end_t: int, end_q: int) -> int:
         assert t < len(T) and q < len(Q), "path leaves the table"
     assert (t, q) == (end_t, end_q), f"path ends at ({t},{q}), not ({end_t},{end_q})"
     return score
+
+
+# --------------------------------------------------------------------------
+# The local extension from an initial score (the BWA-MEM variant)
+# --------------------------------------------------------------------------
+
+def brute_force_H_local(T, Q, p: Dict, h0: int) -> Dict[Tuple[int, int], int]:
+    """Best score of every band cell over the paths that start at the origin
+    with score h0 and whose score is positive after every move (tiny inputs).
+
+    Moves and gap costs are those of ``brute_force_H``; a path whose score
+    reaches zero or below is dropped, so a cell no path reaches is absent.
+    Knows nothing of the E/F/E2/F2 recurrence or of its floors at zero.
+    """
+    p = normalise(p)
+    tlen, qlen = len(T), len(Q)
+    w = eff_w(p, tlen, qlen)
+    best: Dict[Tuple[int, int], int] = {}
+    sys.setrecursionlimit(10000)
+
+    def ok(t, q):
+        if t >= tlen or q >= qlen:
+            return False
+        if t < 0 or q < 0:
+            return True
+        return abs(t - q) <= w
+
+    def visit(t, q, closed, run_dir, run_len):
+        score = closed - (gap(p, run_len) if run_len else 0)
+        if score <= 0:
+            return
+        if t >= 0 and q >= 0 and score > best.get((t, q), MINUS_INF):
+            best[(t, q)] = score
+        if ok(t + 1, q + 1) and t + 1 >= 0 and q + 1 >= 0:
+            s = p["a"] if T[t + 1] == Q[q + 1] else -p["b"]
+            visit(t + 1, q + 1, score + s, None, 0)
+        for d, (dt, dq) in (("D", (1, 0)), ("I", (0, 1))):
+            nt, nq = t + dt, q + dq
+            if not ok(nt, nq):
+                continue
+            if run_dir == d:
+                visit(nt, nq, closed, d, run_len + 1)
+            else:
+                visit(nt, nq, score, d, 1)
+
+    visit(-1, -1, h0, None, 0)
+    return best
+
+
+def scan_rows_local(H: Dict[Tuple[int, int], int], tlen: int, qlen: int, p: Dict,
+                    h0: int) -> Dict:
+    """Apply the local variant's row-by-row rules (one query position at a
+    time) to a table of positive band scores (absent: no live path)."""
+    p = normalise(p)
+    res = dict(max=h0, qe=-1, te=-1, gscore=NEG_OUT, mqe=NEG_OUT, mqe_t=-1,
+               mte=NEG_OUT, mte_q=-1, cells=0, zdropped=0, reach_end=0)
+    if tlen == 0 or qlen == 0:
+        return res
+    w = eff_w(p, tlen, qlen)
+    best, bt, bq = h0, -1, -1
+    mqe = mte = None
+    zdropped = 0
+    for q in range(qlen):
+        ts = [t for t in range(tlen) if abs(t - q) <= w]
+        if not ts:
+            zdropped = 1
+            break
+        res["cells"] += len(ts)
+        row, rt = 0, -1
+        for t in ts:                        # ascending t: the first of equal maxima
+            v = H.get((t, q), 0)
+            if v > row:
+                row, rt = v, t
+        v = H.get((tlen - 1, q), 0)
+        if ts[-1] == tlen - 1 and v > 0 and (mte is None or v > mte):
+            mte, res["mte_q"] = v, q
+        if q == qlen - 1 and row > 0:
+            mqe, res["mqe_t"] = row, rt
+        if row == 0:
+            zdropped = 1
+            break
+        if row > best:
+            best, bt, bq = row, rt, q
+        elif p["zdrop"] >= 0:
+            l = abs((q - bq) - (rt - bt))
+            if best - row > p["zdrop"] + l * p["e2"]:
+                zdropped = 1
+                break
+        if q == qlen - 1 and ts[-1] == tlen - 1 and v > 0:
+            res["gscore"] = v
+    res.update(max=best, te=bt, qe=bq, zdropped=zdropped)
+    if mqe is not None:
+        res["mqe"] = mqe
+    if mte is not None:
+        res["mte"] = mte
+    res["reach_end"] = int(not zdropped and mqe is not None and mqe + p["end_bonus"] > best)
+    return res

@@ -127,9 +127,9 @@ def test_unmutated_oracle_passes_corpus(corpus):
 def test_mutant_is_caught(name, corpus):
     old, new = MUTANTS[name]
     src = open(SRC).read()
-    # the mistakes are planted in the score path, ahead of the traceback
-    # section (which repeats some of the boundary lines)
-    cut = src.index("Traceback of one extension")
+    # the mistakes are planted in the score path (orc_align_pair), ahead of
+    # the local variant and the traceback (which repeat some of its lines)
+    cut = src.index("Local extension from an initial score")
     head, tail = src[:cut], src[cut:]
     assert head.count(old) == 1, f"mutation site for {name} not found exactly once"
     with tempfile.TemporaryDirectory() as d:
