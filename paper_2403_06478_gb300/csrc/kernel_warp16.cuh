@@ -126,7 +126,12 @@ struct Xchg16 {
 // slots 32kC .. 32(k+1)C - 1 of the frame; after every anti-diagonal the warps
 // exchange their edge gap states and anti-diagonal maxima through shared
 // memory and a named barrier, so that the termination test stays exact.
-template <int C, bool DMREG, bool DEFER = false, bool DIR = false, bool SCORE = !DIR, int K = 1>
+// FHEAD: the head runs on the bulk step where the pair allows it.  EDEFER:
+// the edge steps defer their arg-max search like the bulk.  (The larger
+// register budget only: the extra state does not fit the smaller one
+// without spills.)
+template <int C, bool DMREG, bool DEFER = false, bool DIR = false, bool SCORE = !DIR, int K = 1,
+          bool FHEAD = false, bool EDEFER = false>
 struct WarpPair16 {
     static_assert(C == 4 || C == 6 || C == 8 || C == 12 || C == 16 || C == 24,
                   "16-bit lanes use 4, 6, 8, 12, 16 or 24 slots per lane");
@@ -163,6 +168,8 @@ struct WarpPair16 {
     uint8_t *dtab;                 // DIR: this lane's bytes of anti-diagonal 0
     int32_t end_t, end_q;          // DIR and SCORE: where the traceback starts (-1: empty)
     int32_t pend_r, pend_m, pend_lm;   // its anti-diagonal (-3: none), maximum, lane maximum
+    uint32_t pend_rb;              // lane bits of its band slots (~0: every slot of the bulk)
+    bool in_head;                  // FHEAD: the pair loop is running head anti-diagonals
     // base windows (2 bits per slot): Tw field jl = T[B + j0 + jl],
     // Qw field jl = Q[r - B - j0 - jl]
     Win Tw, Qw;
@@ -397,7 +404,8 @@ struct WarpPair16 {
             const uint32_t x0 = ((pend_r - w) & 1) ? L0LO : 0u;   // slot 0 of lane 0 on odd ones
             uint32_t ne = 0;
 #pragma unroll
-            for (int p = 0; p < P; ++p) ne += __vminu2((Hsave[p] ^ mh2) | (p == 0 ? x0 : 0u), 0x10001u) << p;
+            for (int p = 0; p < P; ++p)
+                ne += __vminu2((Hsave[p] ^ mh2) | (p == 0 ? x0 : 0u) | ~half_mask_rt(pend_rb, p), 0x10001u) << p;
             const uint32_t eq = ~ne & ((((1u << P) - 1) << 16) | ((1u << P) - 1));
             const uint32_t lo_eq = eq & 0xffffu, hi_eq = eq >> 16;
             const int32_t jl = lo_eq ? __ffs(lo_eq) - 1 : P + __ffs(hi_eq) - 1;
@@ -410,14 +418,31 @@ struct WarpPair16 {
         }
     }
 
-    // lm: the lane's maximum; m_grp (K > 1): the group's, from exchange().
+    // Head on the bulk step, when a virtual cell may hold the anti-diagonal
+    // maximum: the maximum and the termination test over the band cells only.
+    template <bool ODD>
+    __device__ __forceinline__ bool head_band_max(int32_t r) {
+        const uint32_t (&Hn)[P] = ODD ? Hod : Hev;
+        const int32_t B = frame(r);
+        const uint32_t rb = table_bits(r);
+        uint32_t lmax = 0;
+#pragma unroll
+        for (int p = 0; p < P; ++p) lmax = __vmaxu2(lmax, half_mask_rt(rb, p) & (Hn[p] - OEp));
+        const int32_t lm = (int32_t)max(lmax & 0xffffu, lmax >> 16);
+        auto excl = [&](int p) { return ~half_mask_rt(rb, p); };
+        return anti_diagonal_max<ODD, decltype(excl), false>(r, B, lm, 0, Hn, excl, rb);
+    }
+
+    // lm: the lane's maximum; m_grp (K > 1): the group's, from exchange();
+    // rb: lane bits of the band slots (edge steps; the search excludes the rest).
     template <bool ODD, typename Excl, bool BULKSTEP = false>
     __device__ __forceinline__ bool anti_diagonal_max(int32_t r, int32_t B, int32_t lm, int32_t m_grp,
-                                                      const uint32_t (&Hn)[P], Excl excl) {
+                                                      const uint32_t (&Hn)[P], Excl excl,
+                                                      uint32_t rb = ~0u) {
         const int32_t m = K == 1 ? __reduce_max_sync(FULL, lm) : m_grp;
         const int32_t mt = to_true(m + oe);
         last_m = m + oe;
-        if constexpr (DEFER && BULKSTEP) {
+        if constexpr (DEFER && (BULKSTEP || EDEFER)) {
             if (mt > gmax) {                   // keep it; locate it when needed
                 gmax = mt;
 #pragma unroll
@@ -425,6 +450,7 @@ struct WarpPair16 {
                 pend_r = r;
                 pend_m = K == 1 ? m : xm_w;
                 pend_lm = lm;
+                pend_rb = rb;
                 if constexpr (K > 1) pend_owner = owner_of(r, m);
                 return false;
             }
@@ -652,7 +678,7 @@ struct WarpPair16 {
                 if (qv > cold.mqe && lane == 0) { cold.mqe = qv; cold.mqe_t = r - (qlen - 1); }
             }
             __syncwarp();
-            if (anti_diagonal_max<ODD>(r, B, lm, m_grp, Hd, [&](int p) { return ~half_mask_rt(rb, p); }))
+            if (anti_diagonal_max<ODD>(r, B, lm, m_grp, Hd, [&](int p) { return ~half_mask_rt(rb, p); }, rb))
                 return true;
             if (set_gs && lane == 0) cold.gscore = gs;
             if (--until_rebase <= 2) {
@@ -720,14 +746,24 @@ struct WarpPair16 {
 
     // Bulk anti-diagonals r ((r - w) even) and r+1; returns 0 to go on, else
     // k+1 when the extension stopped on r+k.
+    // FHEAD, in the head: 3 (4) when a virtual cell may hold the maximum of
+    // r (r + 1), the step's own decision undone; the caller decides again
+    // over the band cells only.
     __device__ __forceinline__ int fast_pair(int32_t r) {
         shift_t();
-        if (step<false, BULK>(r)) return 1;
+        const bool s1 = step<false, BULK>(r);
+        if (FHEAD && in_head && last_m == to_u(-gap_cost(prm, r + 2))) { zdropped = 0; return 3; }
+        if (s1) return 1;
         shift_q();
-        if (step<true, BULK>(r + 1)) return 2;
+        const bool s2 = step<true, BULK>(r + 1);
+        if (FHEAD && in_head && last_m == to_u(-gap_cost(prm, r + 3))) { zdropped = 0; return 4; }
+        if (s2) return 2;
         until_rebase -= 2;
         if (until_rebase <= 2) {
-            rebase(last_m, r + 1);
+            if (FHEAD && in_head)          // cells beyond the virtual ones are neither reset nor checked
+                rebase(last_m, r + 1, table_bits(r + 1) | virtual_bits(r + 1), table_bits(r) | virtual_bits(r));
+            else
+                rebase(last_m, r + 1);
             if (ovf) return 2;
         }
         return 0;
@@ -821,6 +857,25 @@ struct WarpPair16 {
         return range_bits(st - B - j0, en - B - j0);
     }
 
+    // Whether the head (anti-diagonals -1 .. w+1) can run on the bulk step:
+    // the table reaches past it on both sides (no last row or column there,
+    // no cell past the end), and the cells beyond the virtual row and column
+    // stay within 16 bits and far below every other score: from minus
+    // infinity they rise by at most a and fall by at most b every two
+    // anti-diagonals, so after w+6 they sit within [NEG - b(w+6)/2 - q2 - e2,
+    // NEG + a(w+6)/2], while the virtual cells and the band's maximum stay
+    // above OFF - K D - gap(w+3) - a(w+3) (the maximum moves by at most D
+    // per anti-diagonal between rebases).
+    __device__ __forceinline__ bool head_on_bulk_step() const {
+        if (min(tlen, qlen) <= w + 2 || w < 4) return false;
+        const int64_t n = w + 6;
+        const int64_t lo = (int64_t)U_NEG - (int64_t)prm.b * n / 2 - oe2;
+        const int64_t hi = (int64_t)U_NEG + (int64_t)prm.a * n / 2;
+        const int64_t floor_virt = (int64_t)OFF - (int64_t)cold.kint * cold.Dp - gap_cost(prm, w + 3) -
+                                   (int64_t)prm.a * (w + 3);
+        return lo > 2 * (int64_t)(prm.a + prm.b + oe2) && hi + 4 * (int64_t)cold.Dp < floor_virt;
+    }
+
     // ------------------------------------------------------------------ pair
     // Returns false if the pair must be recomputed with int32 lanes.
     // DIR (fused): dt is the pair's direction table, one row per anti-diagonal
@@ -893,6 +948,7 @@ struct WarpPair16 {
         }
         gmax = 0;
         pend_r = -3;
+        pend_rb = ~0u;
         if (leader()) {
             cold.mqe = K_NEG_OUT; cold.mqe_t = -1; cold.mte = K_NEG_OUT; cold.mte_q = -1;
             cold.gscore = K_NEG_OUT;
@@ -907,19 +963,52 @@ struct WarpPair16 {
         init_windows(r, tph, qph);
         bool stop = head_step(r);
         const int32_t head_end = min(last_r, w + 1);
-        while (!stop && r < head_end) {
-            ++r;
-            advance(r);
-            stop = head_step(r);
-        }
         // bulk: pairs starting at r = w + 2 ((r - w) even) while every band
         // cell of the pair is a real cell away from the last row and column
         const int32_t L = min(tlen, qlen);
         const int32_t bulk_last = 2 * L - 3 - w;
-        if (use_fast && !stop && r == w + 1) {
+        int32_t limit = INT_MIN;          // the pair loop runs anti-diagonals up to here
+        in_head = false;
+        if (FHEAD && DEFER && K == 1 && use_fast && head_on_bulk_step()) {
+            // The head on the bulk step, in the same pair loop as the bulk.
+            // The virtual row (t = -1) and column (q = -1) then come out of
+            // the recurrence itself, exactly, from the origin the first step
+            // placed; cells beyond them (t < -1 or q < -1) never feed a cell
+            // of the table or a virtual cell and stay far below both (checked
+            // per pair by head_on_bulk_step).  The pair loop covers the head
+            // anti-diagonals from the first with (r - w) even up to w - 3;
+            // the masked step runs the others: r = w - 1, where the virtual
+            // cells (-1, w) and (w, -1) sit in slot 0 and slot w + 1 outside
+            // the band, r = w, which takes (w, -1) from beyond the frame when
+            // w + 1 is its last slot, and the few around them.
+            const int32_t ha = ((-1 - w) & 1) ? 0 : -1;
+            while (!stop && r < ha - 1) {
+                ++r;
+                advance(r);
+                stop = head_step(r);
+            }
+            in_head = true;
+            limit = w - 3;
+        } else {
+            while (!stop && r < head_end) {
+                ++r;
+                advance(r);
+                stop = head_step(r);
+            }
+            if (use_fast && !stop && r == w + 1) limit = bulk_last;
+        }
+        for (;;) {
             const int32_t r0 = r;
-            while (r + 2 <= bulk_last) {
+            while (!stop && r + 2 <= limit) {
                 const int st = fast_pair(r + 1);
+                if (st >= 3) {
+                    // a virtual cell may hold the maximum of r + st - 2: the
+                    // maximum and the termination test over its band cells
+                    r += st - 2;
+                    until_rebase -= st - 2;
+                    stop = ((r - w) & 1) ? head_band_max<true>(r) : head_band_max<false>(r);
+                    break;
+                }
                 if (st) {
                     r += st;          // stopped (Z-drop or 16-bit overflow) on r+st
                     stop = true;
@@ -927,11 +1016,29 @@ struct WarpPair16 {
                 }
                 r += 2;
             }
+            if (FHEAD && in_head) {
+                in_head = false;
+                // head anti-diagonals r0+1 .. r hold r' + 1 band cells each
+                if (leader() && r > r0)
+                    cold.cells += ((int64_t)r + 1) * (r + 2) / 2 - ((int64_t)r0 + 1) * (r0 + 2) / 2;
+                // the rest of the head on the masked step
+                while (!stop && r < head_end) {
+                    ++r;
+                    advance(r);
+                    stop = head_step(r);
+                }
+                if (!stop && r == w + 1) {
+                    limit = bulk_last;
+                    continue;
+                }
+                break;
+            }
             locate_pending();
             // every bulk anti-diagonal holds the whole band: w + 1 cells when
             // (r - w) is even, w when it is odd; the first one is even
             const int32_t nb = r - r0;
-            if (leader()) cold.cells += (int64_t)(nb >> 1) * (2 * w + 1) + (int64_t)(nb & 1) * (w + 1);
+            if (leader() && nb > 0) cold.cells += (int64_t)(nb >> 1) * (2 * w + 1) + (int64_t)(nb & 1) * (w + 1);
+            break;
         }
         while (!stop && r < last_r) {     // r > w + 1 here
             ++r;
@@ -939,6 +1046,7 @@ struct WarpPair16 {
             stop = tail_step(r);
         }
         if (ovf) return false;
+        locate_pending();
         if constexpr (DIR) {
             // the traceback's start: the query end when reached, else the maximum
             const bool reach = !zdropped && cold.mqe != K_NEG_OUT && cold.mqe + prm.end_bonus > gmax;
@@ -1068,7 +1176,11 @@ warp16_align_kernel(const DevBatch *__restrict__ d_batch, int32_t use_fast, int3
         if (k >= L.end) break;
         const int32_t pair = L.items ? L.items[k] : k;
         if (!L.items && (!pair_valid(B, pair) || !warp_takes(B, pair))) continue;
-        WarpPair16<C, (MINB < 4 && C <= 16) || MINB < 3, true> wp(cold[threadIdx.x >> 5]);
+        // the larger register budget of each slot count: 4 blocks per SM for
+        // 4 slots per lane, 2 for 24, 3 otherwise
+        constexpr bool HIGH = C == 4 ? MINB == 4 : (C == 24 ? MINB == 2 : MINB == 3);
+        WarpPair16<C, (MINB < 4 && C <= 16) || MINB < 3, true, false, true, 1, HIGH, HIGH> wp(
+            cold[threadIdx.x >> 5]);
         if (!wp.run(B, pair, lane, use_fast != 0) && lane == 0) {
             const int32_t slot = atomicAdd(&B.counters[CTR_NOVF], 1);
             B.ovf_list[slot] = pair;
