@@ -269,6 +269,131 @@ def traceback_cells(res, batch):
     return total
 
 
+# local extension (the BWA-MEM variant): the int32 cell update (13), the
+# row accumulator riding with E (max and its t: 2) and the floors of the
+# four gap states at zero (4)
+OPS_PER_CELL_LOCAL = 19.0
+
+
+def run_local(args):
+    """The BWA-MEM variant of the extension through agatha_align_batch_local:
+    local extension of every pair from its seed score (uniform 19-60, the
+    workload module's seed_scores), one query row at a time.
+
+    value = cells / local-kernel time (CUDA events the library records
+    around the kernel on the call's stream); e2e = the same cells / the whole
+    call from pinned host buffers (copies both ways included).  Weak scaling
+    under torchrun like the score path."""
+    import torch
+    from paper_2403_06478_gb300 import agatha as A
+    from paper_2403_06478_gb300 import build as B
+    from paper_2403_06478_gb300 import shard as S
+    from paper_2403_06478_gb300 import workload as W
+    rank, world, local = _env_int("RANK", 0), _env_int("WORLD_SIZE", 1), _env_int("LOCAL_RANK", 0)
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    B.build()
+    batch = W.make_config(args.workload, seed=None if rank == 0 else W.SEED_BASE + 2 + 1000 * rank)
+    h0 = W.seed_scores(batch.n_pairs, seed=None if rank == 0 else W.SEED_BASE + 8 + 1000 * rank)
+    pb = A.pack_batch(batch)
+    pin = {k: torch.from_numpy(getattr(pb, k)).pin_memory() for k in
+           ("q_packed", "t_packed", "q_off", "t_off", "q_len", "t_len")}
+    pin_pb = A.PackedBatch(*[pin[k].numpy() for k in
+                             ("q_packed", "t_packed", "q_off", "t_off", "q_len", "t_len")])
+    h0_pin = torch.from_numpy(h0).pin_memory().numpy()
+    n = pb.n_pairs
+    host_out = torch.empty(n * 48, dtype=torch.uint8).pin_memory().numpy().view(A.RESULT_DTYPE)
+    stream = torch.cuda.Stream()
+    torch.cuda.set_stream(stream)
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device="cuda")
+    ctx = A.Context(local, timing=True)
+    for _ in range(args.warmup):
+        ctx.align_local(pin_pb, batch.scoring, h0_pin, stream=stream.cuda_stream, out=host_out)
+    torch.cuda.synchronize()
+    if dist is not None:
+        dist.barrier()
+    torch.cuda.synchronize()
+    sampler = ClockSampler(local)
+    sampler.start()
+    k_ms, e2e_ms = [], []
+    for k in range(args.steps):
+        flush.fill_(k & 0xff)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        ctx.align_local(pin_pb, batch.scoring, h0_pin, stream=stream.cuda_stream, out=host_out)
+        e1.record(stream)
+        e1.synchronize()
+        e2e_ms.append(e0.elapsed_time(e1))
+        k_ms.append(ctx.last_kernel_ms())
+    torch.cuda.synchronize()
+    clocks = sampler.stop()
+    res = host_out.copy()
+    cells = int(res["cells"].sum())
+    (all_cells, all_pairs), (k_tot, e2e_tot) = S.reduce_step_stats(
+        [cells, n], [sum(k_ms), sum(e2e_ms)], device="cuda")
+    if rank != 0:
+        ctx.close()
+        if dist is not None:
+            dist.destroy_process_group()
+        return 0
+    peaks, peak_kind = measured_peaks()
+    n_sm = torch.cuda.get_device_properties(local).multi_processor_count
+    sm_max_mhz = float(peaks.get("sm_max_mhz", 2070.0))
+    int_peak = n_sm * 128 * sm_max_mhz * 1e6 / 1e12
+    t_ms = statistics.mean(k_ms)
+    achieved = cells * OPS_PER_CELL_LOCAL / (t_ms / 1e3) / 1e12
+    w = batch.scoring.w
+    C = next(c for c in (4, 8, 16) if 32 * c - 1 >= w)
+    line = {
+        "metric": "GCUPS of the local extension from seed scores (BWA-MEM variant), exact",
+        "value": round(all_cells * args.steps / (k_tot / 1e3) / 1e9, 3), "unit": "GCUPS", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(k_tot / args.steps, 3),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int32",
+        "data": "synthetic",
+        "config": {"workload": WORKLOADS[args.workload], "pairs_per_gpu": n, "cells_per_step": cells,
+                   "h0": "seed scores uniform in [19, 60]", "l2": "flushed between steps (512 MB write)",
+                   "value_basis": "local kernel, CUDA events on the call's stream"},
+        "pairs_per_s": round(all_pairs * args.steps / (k_tot / 1e3), 1),
+        "zdropped": int(res["zdropped"].sum()), "reach_end": int(res["reach_end"].sum()),
+        "e2e": {"value": round(all_cells * args.steps / (e2e_tot / 1e3) / 1e9, 3), "unit": "GCUPS",
+                "h2d_bytes_per_step": int(pin_pb.nbytes() + 4 * n), "d2h_bytes_per_step": int(n * 48 + 64),
+                "ms_per_step": round(e2e_tot / args.steps, 3)},
+        "gpu_launches": args.steps * 4,          # prep classify / scan / scatter, local kernel
+        "roofline": {"bound": "alu", "achieved": round(achieved, 3), "peak": round(int_peak, 3),
+                     "unit": "Tops/s", "frac": round(achieved / int_peak, 4), "traffic": None,
+                     "kernel": f"local_align_kernel<{C}>", "kernel_ms": round(t_ms, 3),
+                     "ops_per_cell": OPS_PER_CELL_LOCAL,
+                     "peak_basis": f"{n_sm} SMs x 128 int32 lanes x {sm_max_mhz:.0f} MHz ({peak_kind})"},
+        "clocks": clocks,
+    }
+    if world == 1 and not args.no_cpu_baseline:
+        from oracle import oracle as O     # the CPU oracle: timed as a reported baseline and checked
+        # the whole batch: about 4e9 cells, a few seconds on the host cores,
+        # and every pair checked against the timed results
+        idx = np.arange(n)
+        cores = os.cpu_count() or 1
+        t0 = time.perf_counter()
+        ref = O.align_batch(batch, idx=idx, threads=cores, h0=h0)
+        dt = time.perf_counter() - t0
+        sub = res[idx]
+        bad = np.flatnonzero(np.any([sub[f] != ref[f] for f in O.COMPARE_FIELDS], axis=0))
+        line["cpu_baseline"] = {"value": round(int(ref["cells"].sum()) / dt / 1e9, 4), "unit": "GCUPS",
+                                "cores": cores, "kind": "oracle",
+                                "sample": f"all {idx.size} pairs ({int(ref['cells'].sum())} cells, {dt:.1f} s)",
+                                "oracle_checked_pairs": int(idx.size), "oracle_exact": bool(bad.size == 0)}
+        line["oracle_exact"] = bool(bad.size == 0)
+        line["oracle_checked_pairs"] = int(idx.size)
+    print(json.dumps(line), flush=True)
+    ctx.close()
+    if dist is not None:
+        dist.destroy_process_group()
+    return 0
+
+
 def run_traceback(args):
     """The path with CIGARs through agatha_align_cigar (host buffers only).
 
@@ -424,6 +549,8 @@ def main():
                     help="--profile-case: kernel path")
     ap.add_argument("--traceback", action="store_true",
                     help="the path with CIGARs: score kernels + traceback kernel")
+    ap.add_argument("--local", action="store_true",
+                    help="the BWA-MEM variant: local extension from seed scores (agatha_align_batch_local)")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     if args.profile_case:
@@ -434,6 +561,8 @@ def main():
         return run_reference(args)
     if args.traceback:
         return run_traceback(args)
+    if args.local:
+        return run_local(args)
 
     import torch
     from paper_2403_06478_gb300 import agatha as A

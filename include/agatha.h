@@ -166,6 +166,39 @@ int agatha_align_batch(agatha_ctx *ctx, const agatha_batch *batch,
                        const agatha_params *params, agatha_result *out,
                        uint32_t flags, void *stream);
 
+/* The BWA-MEM variant of the extension (paper Section 5.9 applies the method
+ * to BWA-MEM's guided alignment; the rules are this library's reading of
+ * BWA-MEM's published seed extension and clipping):
+ *   - each pair continues an alignment whose score so far is h0[i] (1 ..
+ *     2^24): the origin (-1,-1) holds h0, the virtual row and column
+ *     h0 - gap(l);
+ *   - a path is kept only while its score stays positive after every move;
+ *     cells no such path reaches are empty (score 0) and a diagonal step out
+ *     of an empty cell stays empty;
+ *   - the termination test runs one query position (row q) at a time: the
+ *     row's best cell (lowest t on ties) becomes the best so far (max, te,
+ *     qe) when strictly higher; otherwise the extension stops when
+ *     max - row_best > zdrop + |(q - qe) - (t_row - te)| * e2 (zdrop < 0:
+ *     off); a row with no positive cell, or no band cell, ends it too
+ *     (zdropped = 1 for either);
+ *   - mqe/mqe_t: the best cell of the last query row; mte/mte_q: the best
+ *     positive cell of the last target base; gscore: cell (tlen-1, qlen-1)
+ *     (each from the rows processed, else AGATHA_NEG_INF / -1);
+ *     reach_end = !zdropped && mqe + end_bonus > max (BWA-MEM's clipping
+ *     rule: the end-to-end alignment is kept unless the local one beats it by
+ *     more than the end bonus); cells: band cells of the rows processed; an
+ *     extension nothing improves returns max = h0, qe = te = -1.
+ * Same batch layout, ownership and flags as agatha_align_batch (h0 follows
+ * AGATHA_DEVICE_PTRS like the other arrays), one warp per pair on int32
+ * lanes, pairs ordered longest first (AGATHA_NO_SORT: input order).  The band
+ * is required: 1 <= w <= 511.
+ * Errors: EINVAL (as agatha_align_batch, and h0 outside [1, 2^24]; for
+ * device batches found by the device check), ENOTSUP (w < 0 or w > 511,
+ * AGATHA_PLAIN), ENOMEM, ECUDA. */
+int agatha_align_batch_local(agatha_ctx *ctx, const agatha_batch *batch,
+                             const agatha_params *params, const int32_t *h0,
+                             agatha_result *out, uint32_t flags, void *stream);
+
 /* Duration in milliseconds of the main alignment kernel of the last batch
  * run on ctx (the warp kernel of the batched path, the block kernel of the
  * plain path), from CUDA events recorded around its launch on its stream.

@@ -123,6 +123,9 @@ _SIGS = {
     "agatha_align_batch": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(agatha_batch),
                                           ctypes.POINTER(agatha_params), ctypes.c_void_p,
                                           ctypes.c_uint32, ctypes.c_void_p]),
+    "agatha_align_batch_local": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(agatha_batch),
+                                                ctypes.POINTER(agatha_params), ctypes.c_void_p,
+                                                ctypes.c_void_p, ctypes.c_uint32, ctypes.c_void_p]),
     "agatha_check_params": (ctypes.c_int, [ctypes.POINTER(agatha_params), ctypes.POINTER(agatha_params)]),
     "agatha_pack_codes": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p]),
     "agatha_pack_ascii": (ctypes.c_int, [ctypes.c_char_p, ctypes.c_int64, ctypes.c_void_p]),
@@ -319,6 +322,25 @@ class Context:
                                       ctypes.c_uint32(flags & ~AGATHA_DEVICE_PTRS),
                                       ctypes.c_void_p(stream) if stream else None)
         _check(rc, self._ptr, "agatha_align_batch")
+        return out
+
+    def align_local(self, pb: PackedBatch, scoring, h0, flags: int = 0, stream: int = 0,
+                    out: Optional[np.ndarray] = None) -> np.ndarray:
+        """agatha_align_batch_local with host arrays: the local extension
+        from the initial scores h0 (one per pair); returns the result records."""
+        n = pb.n_pairs
+        if out is None:
+            out = np.zeros(n, dtype=RESULT_DTYPE)
+        h = np.ascontiguousarray(h0, dtype=np.int32)
+        if h.shape[0] != n:
+            raise ValueError("one initial score per pair")
+        b = _host_batch(pb)
+        p = make_params(scoring)
+        rc = lib().agatha_align_batch_local(self._ptr, ctypes.byref(b), ctypes.byref(p),
+                                            h.ctypes.data if n else None, out.ctypes.data if n else None,
+                                            ctypes.c_uint32(flags & ~AGATHA_DEVICE_PTRS),
+                                            ctypes.c_void_p(stream) if stream else None)
+        _check(rc, self._ptr, "agatha_align_batch_local")
         return out
 
     def align_cigar(self, pb: PackedBatch, scoring, flags: int = 0, stream: int = 0,

@@ -49,6 +49,7 @@ struct DevBatch {
     int32_t *wide_order;     // pairs whose band is too wide for the warp kernel
     int64_t *bucket_hist;    // scratch for the ordering
     int32_t *ovf_list;       // pairs the 16-bit kernel hands back to the 32-bit one
+    const int32_t *h0;       // local extension: the initial score of each pair (else null)
     DevParams params;
     int32_t warp_w_max;      // widest band the warp kernel takes (32*C - 1)
     int32_t pad;
@@ -100,6 +101,10 @@ __host__ __device__ inline int32_t class_of_cells(uint64_t est) {
 __host__ __device__ inline uint64_t predicted_cells(int32_t tlen, int32_t qlen, int32_t w) {
     return (uint64_t)(tlen + qlen) * (uint64_t)(w + 1) / 2 + 1;
 }
+
+// Largest initial score of the local extension (keeps every score in int32
+// beside the length bound of pair_valid).
+constexpr int32_t LOCAL_H0_MAX = 1 << 24;
 
 // device error codes written to counters[CTR_ERR]
 enum : int32_t { DEV_ERR_NONE = 0, DEV_ERR_BAD_PAIR = 1 };
@@ -272,6 +277,9 @@ cudaError_t launch_cigar_gather(const TbItem *items, int32_t n_items, const int3
                                 int n_blocks, cudaStream_t s);
 cudaError_t launch_plain_kernel(const DevBatch *d_batch, int64_t n_blocks, int32_t w_max,
                                 int use_wide_list, cudaStream_t s);
+// The local extension (kernel_local.cu), C slots per lane of int32 lanes.
+cudaError_t launch_local(int C, const DevBatch *d_batch, int n_blocks, cudaStream_t s);
+int local_occupancy(int C);
 int plain_kernel_max_w();
 cudaError_t plain_kernel_prepare();
 

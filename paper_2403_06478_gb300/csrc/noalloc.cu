@@ -135,6 +135,7 @@ extern "C" int agatha_align_batch_noalloc(const agatha_batch *batch, const agath
     desc.wide_order = (int32_t *)(ds->scratch + kOffWide);
     desc.bucket_hist = (int64_t *)(ds->scratch + kOffHist);
     desc.ovf_list = nullptr;          // the 32-bit kernel never hands pairs back
+    desc.h0 = nullptr;
     desc.params = p;
     desc.warp_w_max = warp_w_max;
     desc.pad = 0;

@@ -473,6 +473,7 @@ void fill_desc(const Slot *sl, DevBatch *d, const DevParams &p, const LaunchPlan
     d->wide_order = (int32_t *)wide_order;
     d->bucket_hist = (int64_t *)sl->hist.ptr;
     d->ovf_list = (int32_t *)ovf_list;
+    d->h0 = nullptr;
     d->params = p;
     d->warp_w_max = lp.plain ? INT32_MAX : lp.warp_w_max;
     d->pad = 0;
@@ -550,6 +551,7 @@ extern "C" void agatha_destroy(agatha_ctx *ctx) {
     if (ctx->stream) cudaStreamSynchronize(ctx->stream);
     slot_release(ctx->ledger, &ctx->main);
     ctx->tb.release(ctx->ledger);
+    ctx->local_h0.release(ctx->ledger);
     if (ctx->ev_tb0) cudaEventDestroy(ctx->ev_tb0);
     if (ctx->ev_tb1) cudaEventDestroy(ctx->ev_tb1);
     if (ctx->tune_ev0) cudaEventDestroy(ctx->tune_ev0);
@@ -572,7 +574,7 @@ namespace agatha {
 // Copy one batch (host arrays) or point at it (device arrays) and write the
 // descriptor of the context's slot for plan lp (ctx->mu held).
 int stage_batch(agatha_ctx *ctx, const agatha_batch *batch, const DevParams &p, agatha_result *out,
-                uint32_t flags, cudaStream_t s, const LaunchPlan &lp) {
+                uint32_t flags, cudaStream_t s, const LaunchPlan &lp, const int32_t *d_h0) {
     const bool dev = (flags & AGATHA_DEVICE_PTRS) != 0;
     const int64_t n = batch->n_pairs;
     cudaError_t e;
@@ -616,6 +618,7 @@ int stage_batch(agatha_ctx *ctx, const agatha_batch *batch, const DevParams &p, 
     d->t_words = batch->t_words;
     d->n_pairs = n;
     fill_desc(sl, d, p, lp, sl->order.ptr, sl->wide_order.ptr, sl->ovf_list.ptr);
+    d->h0 = d_h0;
     if ((e = cudaMemcpyAsync(sl->d_desc, d, sizeof(DevBatch), cudaMemcpyHostToDevice, s)) != cudaSuccess)
         return cuda_fail(ctx, e, "copy descriptor");
     sl->last_stream = s;

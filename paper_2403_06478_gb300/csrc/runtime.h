@@ -144,7 +144,7 @@ void serve_free(agatha_ctx *ctx);
 // Copy (host arrays) or reference (device arrays) one batch on the context's
 // own slot and write its descriptor for plan lp, without launching anything.
 int stage_batch(agatha_ctx *ctx, const agatha_batch *batch, const DevParams &p, agatha_result *out,
-                uint32_t flags, cudaStream_t s, const LaunchPlan &lp);
+                uint32_t flags, cudaStream_t s, const LaunchPlan &lp, const int32_t *d_h0 = nullptr);
 // The int32 kernel over the 16-bit kernels' hand-back list of the slot's batch.
 cudaError_t launch_overflow_int32(const Slot *sl, const LaunchPlan &lp, cudaStream_t s);
 // Stage one batch on the context's own slot and run it with plan lp; ev0/ev1
@@ -181,6 +181,7 @@ struct agatha_ctx {
     std::map<std::string, agatha::TuneChoice> tune_table;
     cudaEvent_t tune_ev0 = nullptr, tune_ev1 = nullptr;
     agatha::TbBufs tb;                 // traceback buffers (agatha_align_cigar)
+    agatha::DevBuf local_h0;           // initial scores of agatha_align_batch_local (host batches)
     cudaEvent_t ev_tb0 = nullptr, ev_tb1 = nullptr;
     bool tb_timed = false;
     float tb_ms = 0.f;                 // traceback kernels of the last call

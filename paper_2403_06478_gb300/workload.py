@@ -289,6 +289,14 @@ def make_short(n_pairs: int = 200_000, seed: Optional[int] = None) -> Batch:
     return _build("short", rng, ql, em, BWA_SCORING)
 
 
+def seed_scores(n_pairs: int, seed: Optional[int] = None, lo: int = 19, hi: int = 60) -> np.ndarray:
+    """Initial scores for the local extension (the BWA-MEM variant): the score
+    of the seed each extension continues.  BWA-MEM seeds are maximal exact
+    matches of at least 19 bases scored +1 per base, so uniform in [lo, hi]."""
+    rng = np.random.default_rng(SEED_BASE + 8 if seed is None else seed)
+    return rng.integers(lo, hi + 1, n_pairs).astype(np.int32)
+
+
 def make_long_ratio(long_frac: float, n_pairs: int = 20_000, long_len: int = 4096,
                     short_len: int = 128, seed: Optional[int] = None) -> Batch:
     """Two-length mix for the load-balancing study (the paper's synthetic
