@@ -174,7 +174,7 @@ struct WarpPair16 {
     // Qw field jl = Q[r - B - j0 - jl]
     Win Tw, Qw;
     uint32_t Tpf, Qpf;
-    int32_t tcnt, qcnt;
+    int32_t wcnt;          // pairs of shifts left in Tpf and Qpf (one count for both)
     int32_t tpos, qpos;    // next prefetch position (bases, word-relative)
     // relative scores
     int32_t base, OFF, last_m;
@@ -298,20 +298,32 @@ struct WarpPair16 {
         qpos = qb + 1;
         Tpf = load_rel(tp, tspan, tpos);
         Qpf = load_rel(qp, qspan, qpos);
-        tpos += 16;
+        // Every pair of anti-diagonals shifts T ((r - w) even) then Q, so one
+        // count serves both words: T reloads on the shift that finds one pair
+        // left, Q on the shift that ends the count.  When the first shift is
+        // a Q shift, T's first word is used for 15 bases only (the 16th is
+        // the first of its next load), which keeps the two in step.
+        tpos += ((r + 1 - w) & 1) ? 15 : 16;
         qpos += 16;
-        tcnt = 16;
-        qcnt = 16;
+        wcnt = 16;
     }
-    __device__ __forceinline__ void shift_t() {
+    __device__ __forceinline__ void shift_t_window() {
         Tw = (Tw >> 2) | ((Win)(Tpf & 3u) << (2 * C - 2));
         Tpf >>= 2;
-        if (--tcnt == 0) { Tpf = load_rel(tp, tspan, tpos); tpos += 16; tcnt = 16; }
     }
-    __device__ __forceinline__ void shift_q() {
+    __device__ __forceinline__ void shift_q_window() {
         Qw = ((Qw << 2) | (Win)(Qpf & 3u)) & WMASK;
         Qpf >>= 2;
-        if (--qcnt == 0) { Qpf = load_rel(qp, qspan, qpos); qpos += 16; qcnt = 16; }
+    }
+    __device__ __forceinline__ void reload_t() { Tpf = load_rel(tp, tspan, tpos); tpos += 16; }
+    __device__ __forceinline__ void reload_q() { Qpf = load_rel(qp, qspan, qpos); qpos += 16; }
+    __device__ __forceinline__ void shift_t() {
+        shift_t_window();
+        if (wcnt == 1) reload_t();
+    }
+    __device__ __forceinline__ void shift_q() {
+        shift_q_window();
+        if (--wcnt == 0) { reload_q(); wcnt = 16; }
     }
     // windows of anti-diagonal r from those of r-1
     __device__ __forceinline__ void advance(int32_t r) {
@@ -422,6 +434,7 @@ struct WarpPair16 {
     // maximum: the maximum and the termination test over the band cells only.
     template <bool ODD>
     __device__ __forceinline__ bool head_band_max(int32_t r) {
+        if (r < 0) return false;       // no band cell yet: nothing to test
         const uint32_t (&Hn)[P] = ODD ? Hod : Hev;
         const int32_t B = frame(r);
         const uint32_t rb = table_bits(r);
@@ -749,12 +762,18 @@ struct WarpPair16 {
     // FHEAD, in the head: 3 (4) when a virtual cell may hold the maximum of
     // r (r + 1), the step's own decision undone; the caller decides again
     // over the band cells only.
+    // The pair's two window shifts share one count test (after the Q shift).
     __device__ __forceinline__ int fast_pair(int32_t r) {
-        shift_t();
+        shift_t_window();
         const bool s1 = step<false, BULK>(r);
-        if (FHEAD && in_head && last_m == to_u(-gap_cost(prm, r + 2))) { zdropped = 0; return 3; }
+        if (FHEAD && in_head && last_m == to_u(-gap_cost(prm, r + 2))) {
+            zdropped = 0;
+            if (wcnt == 1) reload_t();          // the T shift's own reload
+            return 3;
+        }
         if (s1) return 1;
-        shift_q();
+        shift_q_window();
+        if (--wcnt == 0) { reload_t(); reload_q(); wcnt = 16; }
         const bool s2 = step<true, BULK>(r + 1);
         if (FHEAD && in_head && last_m == to_u(-gap_cost(prm, r + 3))) { zdropped = 0; return 4; }
         if (s2) return 2;
