@@ -502,12 +502,39 @@ struct WarpPair16 {
     // H of the band slot j (the same j in every lane) of the anti-diagonal
     // just computed, read from the lane that owns it.
     __device__ __forceinline__ int32_t slot_value(const uint32_t (&Hn)[P], int32_t j) const {
-        const int32_t local = j % C, pl = local % P;
-        uint32_t v = Hn[0];
+        const int32_t local = j % C;
+        return __shfl_sync(FULL, half_of(reg_select(Hn, local % P), local), (j / C) & 31);
+    }
+    // Register pl of Hn (pl may differ between lanes): a select tree on the
+    // bits of pl, P - 1 selects.
+    __device__ __forceinline__ static uint32_t reg_select(const uint32_t (&Hn)[P], int32_t pl) {
+        uint32_t v[P];
 #pragma unroll
-        for (int p = 1; p < P; ++p) v = pl == p ? Hn[p] : v;
-        const int32_t h = local >= P ? (int32_t)(v >> 16) : (int32_t)(v & 0xffffu);
-        return __shfl_sync(FULL, h, (j / C) & 31);
+        for (int p = 0; p < P; ++p) v[p] = Hn[p];
+#pragma unroll
+        for (int b = 1; b < P; b <<= 1) {
+            const bool hi = (pl & b) != 0;
+#pragma unroll
+            for (int p = 0; p + b < P; p += 2 * b) v[p] = hi ? v[p + b] : v[p];
+        }
+        return v[0];
+    }
+    __device__ __forceinline__ static int32_t half_of(uint32_t v, int32_t local) {
+        return local >= P ? (int32_t)(v >> 16) : (int32_t)(v & 0xffffu);
+    }
+    // H of slots jt and jq (each the same in every lane) at once: every lane
+    // selects the slot it owns (jt where it owns both) and each value is one
+    // shuffle from its owner; a second pass only when one lane owns both and
+    // they differ.
+    __device__ __forceinline__ void slot_values(const uint32_t (&Hn)[P], int32_t jt, int32_t jq, int32_t &vt,
+                                                int32_t &vq) const {
+        const int32_t lt = (jt / C) & 31, lq = (jq / C) & 31;
+        const int32_t j = lane == lt ? jt : jq;
+        const int32_t local = j % C;
+        const int32_t h = half_of(reg_select(Hn, local % P), local);
+        vt = __shfl_sync(FULL, h, lt);
+        if (lt == lq && jt != jq) vq = slot_value(Hn, jq);
+        else vq = __shfl_sync(FULL, h, lq);
     }
     // K > 1: the warp of the group that holds frame slot j
     __device__ __forceinline__ static int32_t slot_warp(int32_t j) { return j / (32 * C); }
@@ -681,14 +708,21 @@ struct WarpPair16 {
             // K warps, the warp holding the slot reads it)
             bool set_gs = false;
             int32_t gs = K_NEG_OUT;
-            if (st <= tlen - 1 && tlen - 1 <= en && (K == 1 || slot_warp(tlen - 1 - B) == wk)) {
-                const int32_t tv = to_true(slot_value(Hd, tlen - 1 - B));
-                if (tv > cold.mte && lane == 0) { cold.mte = tv; cold.mte_q = r - (tlen - 1); }
-                if (r == last_r) { gs = tv; set_gs = true; }   // kept unless Z-drop stops r
-            }
-            if (st <= r - qlen + 1 && r - qlen + 1 <= en && (K == 1 || slot_warp(r - qlen + 1 - B) == wk)) {
-                const int32_t qv = to_true(slot_value(Hd, r - qlen + 1 - B));
-                if (qv > cold.mqe && lane == 0) { cold.mqe = qv; cold.mqe_t = r - (qlen - 1); }
+            const int32_t jt = tlen - 1 - B, jq = r - qlen + 1 - B;
+            const bool at_t = st <= tlen - 1 && tlen - 1 <= en && (K == 1 || slot_warp(jt) == wk);
+            const bool at_q = st <= r - qlen + 1 && r - qlen + 1 <= en && (K == 1 || slot_warp(jq) == wk);
+            if (at_t || at_q) {
+                int32_t hv_t, hv_q;
+                slot_values(Hd, at_t ? jt : jq, at_q ? jq : jt, hv_t, hv_q);
+                if (at_t) {
+                    const int32_t tv = to_true(hv_t);
+                    if (tv > cold.mte && lane == 0) { cold.mte = tv; cold.mte_q = r - (tlen - 1); }
+                    if (r == last_r) { gs = tv; set_gs = true; }   // kept unless Z-drop stops r
+                }
+                if (at_q) {
+                    const int32_t qv = to_true(hv_q);
+                    if (qv > cold.mqe && lane == 0) { cold.mqe = qv; cold.mqe_t = r - (qlen - 1); }
+                }
             }
             __syncwarp();
             if (anti_diagonal_max<ODD>(r, B, lm, m_grp, Hd, [&](int p) { return ~half_mask_rt(rb, p); }, rb))
@@ -697,8 +731,14 @@ struct WarpPair16 {
             if (--until_rebase <= 2) {
                 // slots off the table (past its end, or holding NEG) are
                 // reset; the virtual cells' values are kept
-                if (MODE == TAIL) rebase(last_m, r, rb, table_bits(r - 1));
-                else rebase(last_m, r, rb | vb, table_bits(r - 1) | virtual_bits(r - 1));
+                if (MODE == TAIL) {
+                    // (a tail step run in the head keeps the virtual cells)
+                    const bool vh = FHEAD && in_head;
+                    rebase(last_m, r, rb | (vh ? virtual_bits(r) : 0u),
+                           table_bits(r - 1) | (vh ? virtual_bits(r - 1) : 0u));
+                } else {
+                    rebase(last_m, r, rb | vb, table_bits(r - 1) | virtual_bits(r - 1));
+                }
             }
             return ovf;
         }
@@ -887,6 +927,17 @@ struct WarpPair16 {
     // per anti-diagonal between rebases).
     __device__ __forceinline__ bool head_on_bulk_step() const {
         if (min(tlen, qlen) <= w + 2 || w < 4) return false;
+        return head_bounds_ok();
+    }
+    // A table that the head reaches past on neither side or one side only
+    // (min(tlen, qlen) <= w + 2): the head up to w - 3 runs the tail step
+    // instead (the same recurrence with the maximum taken over table cells
+    // only, and the last row and column read), under the same bounds.
+    __device__ __forceinline__ bool head_on_tail_step() const {
+        if (min(tlen, qlen) > w + 2 || w < 8) return false;
+        return head_bounds_ok();
+    }
+    __device__ __forceinline__ bool head_bounds_ok() const {
         const int64_t n = w + 6;
         const int64_t lo = (int64_t)U_NEG - (int64_t)prm.b * n / 2 - oe2;
         const int64_t hi = (int64_t)U_NEG + (int64_t)prm.a * n / 2;
@@ -1008,6 +1059,31 @@ struct WarpPair16 {
             }
             in_head = true;
             limit = w - 3;
+        } else if (FHEAD && DEFER && K == 1 && use_fast && head_on_tail_step()) {
+            // The head of a short table: the virtual row and column again
+            // come out of the recurrence (as on the bulk step above) up to
+            // w - 3, where the tail step's maximum over table cells leaves
+            // them out; the masked step runs the rest of the head.
+            const int32_t ha = ((-1 - w) & 1) ? 0 : -1;
+            while (!stop && r < ha - 1) {
+                ++r;
+                advance(r);
+                stop = head_step(r);
+            }
+            in_head = true;
+            const int32_t hz = min(w - 3, last_r);
+            while (!stop && r < hz) {
+                ++r;
+                advance(r);
+                stop = tail_step(r);
+            }
+            in_head = false;
+            while (!stop && r < head_end) {
+                ++r;
+                advance(r);
+                stop = head_step(r);
+            }
+            if (use_fast && !stop && r == w + 1) limit = bulk_last;
         } else {
             while (!stop && r < head_end) {
                 ++r;
