@@ -116,6 +116,43 @@ __device__ __forceinline__ int32_t gap_cost(const DevParams &p, int32_t l) {
     return min(p.q + l * p.e, p.q2 + l * p.e2);
 }
 
+// Band cells of anti-diagonals 0..R of a table (tlen x qlen, effective
+// half-width w), R <= tlen + qlen - 2 and the band still inside the table up
+// to R: the sum over r of en(r) - st(r) + 1 with en = min(tlen - 1, r,
+// floor((r + w) / 2)) and st = max(0, r - qlen + 1, ceil((r - w) / 2)), in
+// closed form (each bound is piecewise linear in r, with floor/ceil halves).
+__host__ __device__ inline int64_t sum_half_floor(int64_t m) {      // sum_{k=0}^{m} floor(k/2)
+    return m < 0 ? 0 : (m * m) / 4;
+}
+__host__ __device__ inline int64_t sum_floor_half(int64_t a, int64_t b, int64_t c) {
+    return b < a ? 0 : sum_half_floor(b + c) - sum_half_floor(a - 1 + c);   // sum_{r=a}^{b} floor((r+c)/2)
+}
+__host__ __device__ inline int64_t band_cells_through(int32_t tlen, int32_t qlen, int32_t w, int32_t R) {
+    if (R < 0) return 0;
+    const int64_t T = tlen - 1, Qm = qlen - 1, W = w, RR = R;
+    // sum of en: r up to w, floor((r + w) / 2) after, until it reaches T at rT
+    const int64_t rT = T <= W ? T : 2 * T - W;
+    const int64_t n = RR < rT - 1 ? RR : rT - 1;
+    int64_t sen = 0;
+    if (n >= 0) sen = n <= W ? n * (n + 1) / 2 : W * (W + 1) / 2 + sum_floor_half(W + 1, n, W);
+    if (RR >= rT) sen += T * (RR - rT + 1);
+    // sum of st: 0, then ceil((r - w) / 2) from w + 1 while qlen - 1 > w,
+    // then r - qlen + 1 (from 2(qlen - 1) - w, or from qlen when qlen - 1 <= w)
+    int64_t sst = 0;
+    if (Qm <= W) {
+        const int64_t m = RR - Qm;
+        if (m > 0) sst = m * (m + 1) / 2;
+    } else {
+        const int64_t rq = 2 * Qm - W;
+        sst = sum_floor_half(W + 1, RR < rq - 1 ? RR : rq - 1, 1 - W);
+        if (RR >= rq) {
+            const int64_t hi = RR - Qm, lo = Qm - W;
+            sst += hi * (hi + 1) / 2 - (lo - 1) * lo / 2;
+        }
+    }
+    return sen - sst + RR + 1;
+}
+
 // Effective half-width: a band wider than the table changes nothing.
 __host__ __device__ inline int32_t effective_w(int32_t w, int32_t tlen, int32_t qlen) {
     int32_t m = tlen > qlen ? tlen : qlen;

@@ -84,8 +84,6 @@ struct Cold16 {
     int32_t mqe, mqe_t, mte, mte_q, gscore;
     int32_t gt, gq;               // cell of the global maximum
     int32_t Dp, LOWCHK, kint;     // step bound, lowest allowed score, rebase interval
-    int32_t pad;
-    int64_t cells;
 };
 
 // What the K warps sharing one pair's band (K > 1) hand each other through
@@ -694,7 +692,6 @@ struct WarpPair16 {
         int32_t m_grp = 0;
         if constexpr (K > 1) m_grp = exchange<!ODD, MODE != BULK>(r, lm);
         if constexpr (MODE == BULK) {
-            // (the band cells of bulk anti-diagonals are counted by run())
             // slots beyond the band sit above every band slot of their lane, so
             // the lowest slot holding the maximum is a band slot; only slot 0 of
             // lane 0 (below the band on odd anti-diagonals) is excluded
@@ -703,7 +700,6 @@ struct WarpPair16 {
         } else {
             if (K == 1 ? __any_sync(FULL, ovf) : ovf) { ovf = true; return true; }
             if (r < 0) return false;
-            if (leader()) cold.cells += en - st + 1;
             // best score on the last target row / the last query column (with
             // K warps, the warp holding the slot reads it)
             bool set_gs = false;
@@ -1023,7 +1019,6 @@ struct WarpPair16 {
             cold.mqe = K_NEG_OUT; cold.mqe_t = -1; cold.mte = K_NEG_OUT; cold.mte_q = -1;
             cold.gscore = K_NEG_OUT;
             cold.gt = -1; cold.gq = -1;
-            cold.cells = 0;
         }
         __syncwarp();
         group_sync();
@@ -1093,7 +1088,6 @@ struct WarpPair16 {
             if (use_fast && !stop && r == w + 1) limit = bulk_last;
         }
         for (;;) {
-            const int32_t r0 = r;
             while (!stop && r + 2 <= limit) {
                 const int st = fast_pair(r + 1);
                 if (st >= 3) {
@@ -1113,9 +1107,6 @@ struct WarpPair16 {
             }
             if (FHEAD && in_head) {
                 in_head = false;
-                // head anti-diagonals r0+1 .. r hold r' + 1 band cells each
-                if (leader() && r > r0)
-                    cold.cells += ((int64_t)r + 1) * (r + 2) / 2 - ((int64_t)r0 + 1) * (r0 + 2) / 2;
                 // the rest of the head on the masked step
                 while (!stop && r < head_end) {
                     ++r;
@@ -1129,10 +1120,6 @@ struct WarpPair16 {
                 break;
             }
             locate_pending();
-            // every bulk anti-diagonal holds the whole band: w + 1 cells when
-            // (r - w) is even, w when it is odd; the first one is even
-            const int32_t nb = r - r0;
-            if (leader() && nb > 0) cold.cells += (int64_t)(nb >> 1) * (2 * w + 1) + (int64_t)(nb & 1) * (w + 1);
             break;
         }
         while (!stop && r < last_r) {     // r > w + 1 here
@@ -1155,7 +1142,11 @@ struct WarpPair16 {
             o.max = gmax; o.te = cold.gt; o.qe = cold.gq;
             o.gscore = cold.gscore; o.mqe = mqe; o.mqe_t = cold.mqe_t; o.mte = cold.mte;
             o.mte_q = cold.mte_q;
-            o.cells = cold.cells;
+            // band cells of anti-diagonals 0 .. r (none on r when the band
+            // left the table there)
+            const int32_t st_r = max(max(0, r - qlen + 1), ceil_div2(r - w));
+            const int32_t en_r = min(min(tlen - 1, r), floor_div2(r + w));
+            o.cells = band_cells_through(tlen, qlen, w, st_r > en_r ? r - 1 : r);
             o.zdropped = (uint8_t)zdropped;
             o.reach_end = (uint8_t)(!zdropped && mqe != K_NEG_OUT && mqe + prm.end_bonus > gmax);
             o.lane16 = 1;
