@@ -74,6 +74,10 @@ extern "C" {
 #define AGATHA_WARPS2      0x400u /* 16-bit kernel with 2 warps sharing each
                                      pair's band (bands of 256..767 slots)   */
 #define AGATHA_WARPS4      0x800u /* the same with 4 warps per pair           */
+#define AGATHA_HALF_WARP   0x1000u /* 16-bit kernel with two pairs per warp,
+                                      16 lanes of 8 slots each (bands up to
+                                      127; AGATHA_ENOTSUP for wider ones,
+                                      AGATHA_EINVAL with WARPS2/WARPS4)     */
 
 /* Flags for agatha_config.flags. */
 #define AGATHA_CFG_TIMING  0x1    /* record CUDA events around the main kernel

@@ -42,6 +42,7 @@ AGATHA_NO_TUNE = 0x100
 AGATHA_TB_TWO_PASS = 0x200
 AGATHA_WARPS2 = 0x400
 AGATHA_WARPS4 = 0x800
+AGATHA_HALF_WARP = 0x1000
 
 AGATHA_CFG_TIMING = 0x1
 AGATHA_CFG_AUTOTUNE = 0x2
@@ -53,7 +54,8 @@ AGATHA_CIGAR_D = 2
 CIGAR_OPS = "MID"
 
 # kernel variants the autotuner chooses between, per length class
-VARIANT_NAMES = ("int16x2", "int16x2-highreg", "int32", "int16x2-2warps", "int16x2-4warps")
+VARIANT_NAMES = ("int16x2", "int16x2-highreg", "int32", "int16x2-2warps", "int16x2-4warps",
+                 "int16x2-halfwarp")
 
 NEG_INF = -0x40000000
 

@@ -283,10 +283,11 @@ cudaError_t launch_warp_c(const DevBatch *d_batch, int n_blocks, cudaStream_t s,
 template <int C>
 int occupancy_warp_c();
 // MINB: resident blocks per SM the 16-bit kernel's registers are cut for.
-template <int C, int MINB>
+// G: lanes per pair (32, or 16 for two pairs per warp).
+template <int C, int MINB, int G = 32>
 cudaError_t launch_warp16_c(const DevBatch *d_batch, int n_blocks, cudaStream_t s, int use_fast,
                             int list = WARP_LIST_MAIN);
-template <int C, int MINB>
+template <int C, int MINB, int G = 32>
 int occupancy_warp16_c();
 // K warps share one pair's band (C slots per lane of each warp).
 template <int C, int K, int MINB>

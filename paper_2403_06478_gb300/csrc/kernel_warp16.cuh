@@ -129,14 +129,27 @@ struct Xchg16 {
 // register budget only: the extra state does not fit the smaller one
 // without spills.)
 template <int C, bool DMREG, bool DEFER = false, bool DIR = false, bool SCORE = !DIR, int K = 1,
-          bool FHEAD = false, bool EDEFER = false>
+          bool FHEAD = false, bool EDEFER = false, int G = 32>
 struct WarpPair16 {
     static_assert(C == 4 || C == 6 || C == 8 || C == 12 || C == 16 || C == 24,
                   "16-bit lanes use 4, 6, 8, 12, 16 or 24 slots per lane");
     static_assert(K == 1 || K == 2 || K == 4, "1, 2 or 4 warps per pair");
     static_assert(K == 1 || !DIR, "the traceback variants run one warp per pair");
+    static_assert(G == 32 || (G == 16 && K == 1 && !DIR), "half-warp pairs: one group, score only");
     static constexpr int P = C / 2;
-    static constexpr int32_t NS = 32 * C * K;     // slots of the frame
+    static constexpr int32_t NS = G * C * K;      // slots of the frame
+    // G lanes per pair: the whole warp, or a half warp (two pairs per warp,
+    // each half with its own mask for every warp-collective operation)
+    __device__ __forceinline__ static uint32_t gmask() {
+        if constexpr (G == 32) return FULL;
+        else return 0xffffu << (threadIdx.x & 16);
+    }
+    // ballot over the pair's lanes, bit i for the pair's lane i
+    __device__ __forceinline__ static uint32_t gballot(bool v) {
+        const uint32_t b = __ballot_sync(gmask(), v);
+        if constexpr (G == 32) return b;
+        else return (b >> (threadIdx.x & 16)) & 0xffffu;
+    }
     // a base window holds 2 bits per slot
     using Win = typename std::conditional<(2 * C > 32), uint64_t, uint32_t>::type;
     static constexpr Win WMASK = (Win)(((uint64_t)1 << (2 * C)) - 1);
@@ -212,7 +225,7 @@ struct WarpPair16 {
     __device__ __forceinline__ bool leader() const { return lane == 0 && (K == 1 || wk == 0); }
     // K > 1: true in every lane of the group if v is true in any lane of any warp
     __device__ __forceinline__ bool group_any(bool v) {
-        const bool w_any = __any_sync(FULL, v);
+        const bool w_any = __any_sync(gmask(), v);
         if constexpr (K == 1) return w_any;
         if (lane == 0) xch->g[wk] = w_any ? 1 : 0;
         group_sync();
@@ -229,8 +242,8 @@ struct WarpPair16 {
     template <bool ODDNEXT, bool FLAG>
     __device__ __forceinline__ int32_t exchange(int32_t r, int32_t lm) {
         const int b = r & 1;
-        const int32_t mw = __reduce_max_sync(FULL, lm);
-        const bool fw = FLAG ? __any_sync(FULL, ovf) : false;
+        const int32_t mw = __reduce_max_sync(gmask(), lm);
+        const bool fw = FLAG ? __any_sync(gmask(), ovf) : false;
         if (lane == 0) {
             xch->m[b][wk] = mw;
             if (FLAG) xch->f[b][wk] = fw ? 1 : 0;
@@ -382,7 +395,7 @@ struct WarpPair16 {
         if (m > gmax) {
             gmax = m;
             if (leader()) { cold.gt = tstar; cold.gq = qstar; }
-            __syncwarp();
+            __syncwarp(gmask());
             return false;
         }
         const int32_t gt = cold.gt, gq = cold.gq;
@@ -408,7 +421,7 @@ struct WarpPair16 {
                 pend_r = -3;
                 return;
             }
-            const unsigned ball = __ballot_sync(FULL, pend_lm == pend_m);
+            const unsigned ball = gballot(pend_lm == pend_m);
             const int src = __ffs(ball) - 1;
             const uint32_t mh2 = (uint32_t)(pend_m + oe) * 0x10001u;
             const uint32_t x0 = ((pend_r - w) & 1) ? L0LO : 0u;   // slot 0 of lane 0 on odd ones
@@ -419,10 +432,10 @@ struct WarpPair16 {
             const uint32_t eq = ~ne & ((((1u << P) - 1) << 16) | ((1u << P) - 1));
             const uint32_t lo_eq = eq & 0xffffu, hi_eq = eq >> 16;
             const int32_t jl = lo_eq ? __ffs(lo_eq) - 1 : P + __ffs(hi_eq) - 1;
-            const int32_t lj = __shfl_sync(FULL, jl, src);
-            const int32_t tstar = frame(pend_r) + (wk * 32 + src) * C + lj;
+            const int32_t lj = __shfl_sync(gmask(), jl, src, G);
+            const int32_t tstar = frame(pend_r) + (wk * G + src) * C + lj;
             if (lane == 0) { cold.gt = tstar; cold.gq = pend_r - tstar; }
-            __syncwarp();
+            __syncwarp(gmask());
             group_sync();
             pend_r = -3;
         }
@@ -450,7 +463,7 @@ struct WarpPair16 {
     __device__ __forceinline__ bool anti_diagonal_max(int32_t r, int32_t B, int32_t lm, int32_t m_grp,
                                                       const uint32_t (&Hn)[P], Excl excl,
                                                       uint32_t rb = ~0u) {
-        const int32_t m = K == 1 ? __reduce_max_sync(FULL, lm) : m_grp;
+        const int32_t m = K == 1 ? __reduce_max_sync(gmask(), lm) : m_grp;
         const int32_t mt = to_true(m + oe);
         last_m = m + oe;
         if constexpr (DEFER && (BULKSTEP || EDEFER)) {
@@ -475,7 +488,7 @@ struct WarpPair16 {
             int32_t tstar = 0;
             const int32_t owner = K == 1 ? 0 : owner_of(r, m);
             if (K == 1 || wk == owner) {
-                const unsigned ball = __ballot_sync(FULL, lm == m);
+                const unsigned ball = gballot(lm == m);
                 const int src = __ffs(ball) - 1;
                 const uint32_t mh2 = (uint32_t)(m + oe) * 0x10001u;
                 uint32_t ne = 0;
@@ -484,8 +497,8 @@ struct WarpPair16 {
                 const uint32_t eq = ~ne & ((((1u << P) - 1) << 16) | ((1u << P) - 1));
                 const uint32_t lo_eq = eq & 0xffffu, hi_eq = eq >> 16;
                 const int32_t jl = lo_eq ? __ffs(lo_eq) - 1 : P + __ffs(hi_eq) - 1;
-                const int32_t lj = __shfl_sync(FULL, jl, src);
-                tstar = B + (wk * 32 + src) * C + lj;
+                const int32_t lj = __shfl_sync(gmask(), jl, src, G);
+                tstar = B + (wk * G + src) * C + lj;
                 if (K > 1 && lane == 0) xch->t[r & 1] = tstar;
             }
             if constexpr (K > 1) {
@@ -501,7 +514,7 @@ struct WarpPair16 {
     // just computed, read from the lane that owns it.
     __device__ __forceinline__ int32_t slot_value(const uint32_t (&Hn)[P], int32_t j) const {
         const int32_t local = j % C;
-        return __shfl_sync(FULL, half_of(reg_select(Hn, local % P), local), (j / C) & 31);
+        return __shfl_sync(gmask(), half_of(reg_select(Hn, local % P), local), (j / C) & (G - 1), G);
     }
     // Register pl of Hn (pl may differ between lanes): a select tree on the
     // bits of pl, P - 1 selects.
@@ -526,16 +539,16 @@ struct WarpPair16 {
     // they differ.
     __device__ __forceinline__ void slot_values(const uint32_t (&Hn)[P], int32_t jt, int32_t jq, int32_t &vt,
                                                 int32_t &vq) const {
-        const int32_t lt = (jt / C) & 31, lq = (jq / C) & 31;
+        const int32_t lt = (jt / C) & (G - 1), lq = (jq / C) & (G - 1);
         const int32_t j = lane == lt ? jt : jq;
         const int32_t local = j % C;
         const int32_t h = half_of(reg_select(Hn, local % P), local);
-        vt = __shfl_sync(FULL, h, lt);
+        vt = __shfl_sync(gmask(), h, lt, G);
         if (lt == lq && jt != jq) vq = slot_value(Hn, jq);
-        else vq = __shfl_sync(FULL, h, lq);
+        else vq = __shfl_sync(gmask(), h, lq, G);
     }
     // K > 1: the warp of the group that holds frame slot j
-    __device__ __forceinline__ static int32_t slot_warp(int32_t j) { return j / (32 * C); }
+    __device__ __forceinline__ static int32_t slot_warp(int32_t j) { return j / (G * C); }
 
     // Step modes.  BULK: every slot in [0, w] is a band cell of the table.
     // HEAD (r <= w + 1): the band meets the table's first row and column;
@@ -572,7 +585,7 @@ struct WarpPair16 {
             if (r + 1 < qlen) vb |= slot_bit(-1 - B - j0);                 // (-1, r+1)
             if (r >= -1 && r + 1 < tlen) vb |= slot_bit(r + 1 - B - j0);  // (r+1, -1)
             const int32_t vv = to_u(r == -2 ? 0 : -gap_cost(prm, r + 2));
-            if (__any_sync(FULL, vb != 0u) && (vv < cold.LOWCHK || vv > 0xffff - cold.Dp)) ovf = true;
+            if (__any_sync(gmask(), vb != 0u) && (vv < cold.LOWCHK || vv > 0xffff - cold.Dp)) ovf = true;
             VVp = (uint32_t)vv * 0x10001u;
         }
         uint32_t edge, edge2;
@@ -581,19 +594,19 @@ struct WarpPair16 {
             // register); for lane 0 it would feed slot 0, outside the band here
             // (with K warps, lane 0 of a later warp takes the word the warp
             // below published)
-            uint32_t eL = __shfl_up_sync(FULL, Eo[P - 1], 1);
-            uint32_t e2L = __shfl_up_sync(FULL, E2o[P - 1], 1);
+            uint32_t eL = __shfl_up_sync(gmask(), Eo[P - 1], 1, G);
+            uint32_t e2L = __shfl_up_sync(gmask(), E2o[P - 1], 1, G);
             if (K > 1 && wk > 0 && lane == 0) { eL = xe0; e2L = xe1; }
             edge = mux(L0LO, NEGp, prmt(eL, Eo[P - 1], 0x5432));
             edge2 = mux(L0LO, NEGp, prmt(e2L, E2o[P - 1], 0x5432));
         } else {
             // F of the last slot from the right lane's first slot (low half of
             // its register 0; with K warps, from the warp above for lane 31)
-            uint32_t fR = __shfl_down_sync(FULL, Fo[0], 1);
-            uint32_t f2R = __shfl_down_sync(FULL, F2o[0], 1);
+            uint32_t fR = __shfl_down_sync(gmask(), Fo[0], 1, G);
+            uint32_t f2R = __shfl_down_sync(gmask(), F2o[0], 1, G);
             if (K > 1 && wk < K - 1 && lane == 31) { fR = xe0; f2R = xe1; }
             uint32_t inj = NEGp, inj2 = NEGp;
-            if (MODE == HEAD && lane == 31 && (K == 1 || wk == K - 1)) {
+            if (MODE == HEAD && lane == G - 1 && (K == 1 || wk == K - 1)) {
                 // beyond the last lane: slot NS of r-1, the virtual column
                 // cell (t, -1) when q == -1 there
                 const int32_t ts = frame(r - 1) + NS, qs = r - 1 - ts;
@@ -698,7 +711,7 @@ struct WarpPair16 {
             auto excl = [&](int p) { return (ODD && p == 0) ? L0LO : 0u; };
             return anti_diagonal_max<ODD, decltype(excl), true>(r, B, lm, m_grp, Hd, excl);
         } else {
-            if (K == 1 ? __any_sync(FULL, ovf) : ovf) { ovf = true; return true; }
+            if (K == 1 ? __any_sync(gmask(), ovf) : ovf) { ovf = true; return true; }
             if (r < 0) return false;
             // best score on the last target row / the last query column (with
             // K warps, the warp holding the slot reads it)
@@ -720,7 +733,7 @@ struct WarpPair16 {
                     if (qv > cold.mqe && lane == 0) { cold.mqe = qv; cold.mqe_t = r - (qlen - 1); }
                 }
             }
-            __syncwarp();
+            __syncwarp(gmask());
             if (anti_diagonal_max<ODD>(r, B, lm, m_grp, Hd, [&](int p) { return ~half_mask_rt(rb, p); }, rb))
                 return true;
             if (set_gs && lane == 0) cold.gscore = gs;
@@ -777,15 +790,15 @@ struct WarpPair16 {
             // fast_pair rebases after the odd step of a pair
             if (ODD && until_rebase <= 4) {
                 const int32_t lm = (int32_t)max(lmax & 0xffffu, lmax >> 16);
-                last_m = __reduce_max_sync(FULL, lm) + oe;
+                last_m = __reduce_max_sync(gmask(), lm) + oe;
             }
             return false;
         } else {
-            if (__any_sync(FULL, ovf)) { ovf = true; return true; }
+            if (__any_sync(gmask(), ovf)) { ovf = true; return true; }
             if (r < 0) return false;
             if (--until_rebase <= 2) {
                 const int32_t lm = (int32_t)max(lmax & 0xffffu, lmax >> 16);
-                last_m = __reduce_max_sync(FULL, lm) + oe;
+                last_m = __reduce_max_sync(gmask(), lm) + oe;
                 if (MODE == TAIL) rebase(last_m, r, rb, table_bits(r - 1));
                 else rebase(last_m, r, rb | vb, table_bits(r - 1) | virtual_bits(r - 1));
             }
@@ -971,7 +984,7 @@ struct WarpPair16 {
         }
         w = effective_w(prm.w, tlen, qlen);
         oe = prm.q + prm.e; oe2 = prm.q2 + prm.e2;
-        j0 = (wk * 32 + lane) * C;
+        j0 = (wk * G + lane) * C;
         last_r = tlen + qlen - 2;
         if constexpr (DIR) dtab = dt + j0;
         {
@@ -997,7 +1010,7 @@ struct WarpPair16 {
         NE2p = ((uint32_t)(-prm.e2) & 0xffffu) * 0x10001u;
         NEGp = U_NEG * 0x10001u;
         L0LO = (lane == 0 && wk == 0) ? 0x0000ffffu : 0u;
-        L31HI = (lane == 31 && wk == K - 1) ? 0xffff0000u : 0u;
+        L31HI = (lane == G - 1 && wk == K - 1) ? 0xffff0000u : 0u;
         xe0 = xe1 = NEGp;
 #pragma unroll
         for (int p = 0; p < P; ++p) {
@@ -1020,7 +1033,7 @@ struct WarpPair16 {
             cold.gscore = K_NEG_OUT;
             cold.gt = -1; cold.gq = -1;
         }
-        __syncwarp();
+        __syncwarp(gmask());
         group_sync();
         zdropped = 0;
 
@@ -1220,7 +1233,7 @@ struct WarpPair16 {
         }
         gmax = 0;
         pend_r = -3;
-        __syncwarp();
+        __syncwarp(gmask());
         zdropped = 0;
         int32_t r = -2;
         init_windows(r, tph, qph);
@@ -1248,28 +1261,56 @@ struct WarpPair16 {
     }
 };
 
-template <int C, int MINB>
+// G = 16: each half warp aligns its own pairs (two pairs per warp), taking
+// them from the queue on its own.
+template <int C, int MINB, int G = 32>
 __global__ void __launch_bounds__(WARP_BLOCK_THREADS, MINB)
 warp16_align_kernel(const DevBatch *__restrict__ d_batch, int32_t use_fast, int32_t list) {
-    __shared__ Cold16 cold[WARP_BLOCK_THREADS / 32];
+    __shared__ Cold16 cold[WARP_BLOCK_THREADS / G];
     const DevBatch B = *d_batch;
-    const int lane = threadIdx.x & 31;
+    const int lane = threadIdx.x & (G - 1);
+    const uint32_t gm = G == 32 ? FULL : 0xffffu << (threadIdx.x & 16);
     const WorkList L = work_list(B, list);
-    for (;;) {
-        int32_t k = 0;
-        if (lane == 0) k = L.begin + atomicAdd(L.head, 1);
-        k = __shfl_sync(FULL, k, 0);
-        if (k >= L.end) break;
-        const int32_t pair = L.items ? L.items[k] : k;
-        if (!L.items && (!pair_valid(B, pair) || !warp_takes(B, pair))) continue;
-        // the larger register budget of each slot count: 4 blocks per SM for
-        // 4 slots per lane, 2 for 24, 3 otherwise
-        constexpr bool HIGH = C == 4 ? MINB == 4 : (C == 24 ? MINB == 2 : MINB == 3);
-        WarpPair16<C, (MINB < 4 && C <= 16) || MINB < 3, true, false, true, 1, HIGH, HIGH> wp(
-            cold[threadIdx.x >> 5]);
-        if (!wp.run(B, pair, lane, use_fast != 0) && lane == 0) {
-            const int32_t slot = atomicAdd(&B.counters[CTR_NOVF], 1);
-            B.ovf_list[slot] = pair;
+    // the larger register budget of each slot count: 4 blocks per SM for
+    // 4 slots per lane, 2 for 24, 3 otherwise
+    constexpr bool HIGH = C == 4 ? MINB == 4 : (C == 24 ? MINB == 2 : MINB == 3);
+    using Pair = WarpPair16<C, (MINB < 4 && C <= 16) || MINB < 3, true, false, true, 1, HIGH, HIGH, G>;
+    if constexpr (G == 32) {
+        for (;;) {
+            int32_t k = 0;
+            if (lane == 0) k = L.begin + atomicAdd(L.head, 1);
+            k = __shfl_sync(gm, k, 0, G);
+            if (k >= L.end) break;
+            const int32_t pair = L.items ? L.items[k] : k;
+            if (!L.items && (!pair_valid(B, pair) || !warp_takes(B, pair))) continue;
+            Pair wp(cold[threadIdx.x / G]);
+            if (!wp.run(B, pair, lane, use_fast != 0) && lane == 0) {
+                const int32_t slot = atomicAdd(&B.counters[CTR_NOVF], 1);
+                B.ovf_list[slot] = pair;
+            }
+        }
+    } else {
+        // The warp takes two neighbouring pairs of the longest-first queue at
+        // once (about the same length), one per half, and both halves start
+        // their next pairs together: the two then pass through the same step
+        // variants at the same time for most of their anti-diagonals.
+        for (;;) {
+            int32_t k0 = 0;
+            if ((threadIdx.x & 31) == 0) k0 = L.begin + atomicAdd(L.head, 2);
+            k0 = __shfl_sync(FULL, k0, 0);
+            if (k0 >= L.end) break;
+            const int32_t k = k0 + (int32_t)((threadIdx.x >> 4) & 1);
+            if (k < L.end) {
+                const int32_t pair = L.items ? L.items[k] : k;
+                if (L.items || (pair_valid(B, pair) && warp_takes(B, pair))) {
+                    Pair wp(cold[threadIdx.x / G]);
+                    if (!wp.run(B, pair, lane, use_fast != 0) && lane == 0) {
+                        const int32_t slot = atomicAdd(&B.counters[CTR_NOVF], 1);
+                        B.ovf_list[slot] = pair;
+                    }
+                }
+            }
+            __syncwarp();
         }
     }
     if (lane == 0) mark_step_end(B.counters);
@@ -1324,17 +1365,17 @@ int occupancy_warp16k_c() {
     return nb > 0 ? nb : 1;
 }
 
-template <int C, int MINB>
+template <int C, int MINB, int G>
 cudaError_t launch_warp16_c(const DevBatch *d_batch, int n_blocks, cudaStream_t s, int use_fast,
                             int list) {
-    warp16_align_kernel<C, MINB><<<n_blocks, WARP_BLOCK_THREADS, 0, s>>>(d_batch, use_fast, list);
+    warp16_align_kernel<C, MINB, G><<<n_blocks, WARP_BLOCK_THREADS, 0, s>>>(d_batch, use_fast, list);
     return cudaGetLastError();
 }
 
-template <int C, int MINB>
+template <int C, int MINB, int G>
 int occupancy_warp16_c() {
     int nb = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, warp16_align_kernel<C, MINB>,
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, warp16_align_kernel<C, MINB, G>,
                                                       WARP_BLOCK_THREADS, 0) != cudaSuccess)
         return 1;
     return nb > 0 ? nb : 1;

@@ -179,6 +179,15 @@ static cudaError_t launch_warp16(int C, int high, const DevBatch *d, int blocks,
     }
 }
 
+// 16-bit kernel with two pairs per warp (16 lanes each) for the band of the
+// C16-slot kernel: 8 slots per lane for the 4-slot band; none for wider ones.
+static cudaError_t launch_warp16h(int C16, const DevBatch *d, int blocks, cudaStream_t s, int fast,
+                                  int list) {
+    if (C16 == 4) return launch_warp16_c<8, 3, 16>(d, blocks, s, fast, list);
+    return cudaErrorInvalidValue;
+}
+int warp16h_occupancy(int C16) { return C16 == 4 ? occupancy_warp16_c<8, 3, 16>() : 0; }
+
 // 16-bit kernel with K warps per pair, for the band of the C16-slot kernel:
 // 2 warps of 8 or 12 slots per lane, 4 warps of 4 or 6.
 static cudaError_t launch_warp16k(int C16, int K, const DevBatch *d, int blocks, cudaStream_t s,
@@ -263,7 +272,10 @@ static cudaError_t enqueue_part(agatha_ctx *ctx, Slot *sl, const LaunchPlan &lp,
     if (lp.plain) return launch_plain_kernel(d, lp.plain_blocks, lp.plain_w, 0, s);
     bool any16 = false;
     if (!lp.split) {
-        if (lp.lane16 && lp.groupk > 1) {
+        if (lp.lane16 && lp.half) {
+            e = launch_warp16h(lp.C16, d, lp.warp16h_blocks, s, lp.fast, WARP_LIST_MAIN);
+            any16 = true;
+        } else if (lp.lane16 && lp.groupk > 1) {
             e = launch_warp16k(lp.C16, lp.groupk, d, lp.warp16k_blocks[lp.groupk == 4], s, lp.fast,
                                WARP_LIST_MAIN);
             any16 = true;
@@ -285,6 +297,9 @@ static cudaError_t enqueue_part(agatha_ctx *ctx, Slot *sl, const LaunchPlan &lp,
             const int v = lp.cls_var[c];
             if (v == VAR_32) {
                 e = launch_warp(lp.C, d, lp.warp_blocks, sc, lp.fast, WARP_LIST_CLASS + c);
+            } else if (v == VAR_16_HALF) {
+                e = launch_warp16h(lp.C16, d, lp.warp16h_blocks, sc, lp.fast, WARP_LIST_CLASS + c);
+                any16 = true;
             } else if (v == VAR_16_K2 || v == VAR_16_K4) {
                 const int K = variant_warps(v);
                 e = launch_warp16k(lp.C16, K, d, lp.warp16k_blocks[K == 4], sc, lp.fast, WARP_LIST_CLASS + c);
@@ -448,6 +463,8 @@ int make_plan(agatha_ctx *ctx, const DevParams &p, const BatchShape &shape, uint
     lp->regs_high = (flags & AGATHA_REGS_HIGH) ? 1 : 0;
     lp->split = 0;
     lp->groupk = 1;
+    lp->half = 0;
+    lp->warp16h_blocks = 0;
     if (lp->lane16) {
         lp->warp_w_max = 32 * lp->C16 - 1;
         lp->warp16_blocks[0] = ctx->n_sm * warp16_occupancy(lp->C16, 0);
@@ -455,10 +472,18 @@ int make_plan(agatha_ctx *ctx, const DevParams &p, const BatchShape &shape, uint
         lp->warp16k_blocks[0] = ctx->n_sm * warp16k_occupancy(lp->C16, 2);
         lp->warp16k_blocks[1] = ctx->n_sm * warp16k_occupancy(lp->C16, 4);
         const int K = (flags & AGATHA_WARPS4) ? 4 : ((flags & AGATHA_WARPS2) ? 2 : 1);
+        if (K > 1 && (flags & AGATHA_HALF_WARP))
+            return set_error(ctx, AGATHA_EINVAL, "two pairs per warp and several warps per pair");
         if (K > 1) {
             if (!lp->warp16k_blocks[K == 4])
                 return set_error(ctx, AGATHA_ENOTSUP, "%d warps per pair need a band of 256 to 767", K);
             lp->groupk = K;
+        }
+        lp->warp16h_blocks = ctx->n_sm * warp16h_occupancy(lp->C16);
+        if (flags & AGATHA_HALF_WARP) {
+            if (!lp->warp16h_blocks)
+                return set_error(ctx, AGATHA_ENOTSUP, "two pairs per warp need a band of at most 127");
+            lp->half = 1;
         }
     }
     lp->plain_w = 0;

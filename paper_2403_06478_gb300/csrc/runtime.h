@@ -57,7 +57,10 @@ using PlanKey = std::array<int32_t, 12>;
 
 // Kernel variant of a length class: 16-bit lanes (one warp per pair, at
 // either register budget, or 2 / 4 warps sharing a pair's band) or int32 lanes.
-enum : int8_t { VAR_16 = 0, VAR_16_HIGHREG = 1, VAR_32 = 2, VAR_16_K2 = 3, VAR_16_K4 = 4, N_VARIANTS = 5 };
+// VAR_16_HALF: two pairs per warp, 16 lanes of 8 slots each (bands up to 127).
+enum : int8_t {
+    VAR_16 = 0, VAR_16_HIGHREG = 1, VAR_32 = 2, VAR_16_K2 = 3, VAR_16_K4 = 4, VAR_16_HALF = 5, N_VARIANTS = 6
+};
 inline int variant_warps(int v) { return v == VAR_16_K2 ? 2 : (v == VAR_16_K4 ? 4 : 1); }
 
 // What the autotuner keeps per key: the variant of each length class and
@@ -78,6 +81,8 @@ struct LaunchPlan {
     int warp16_blocks[2] = {0, 0};   // grid of the 16-bit kernel per budget
     int groupk = 1;             // warps per pair of the single launch (1, 2, 4)
     int warp16k_blocks[2] = {0, 0};  // grids of the 2- and 4-warp kernels (0: none)
+    int half = 0;               // the single launch runs two pairs per warp
+    int warp16h_blocks = 0;     // grid of that kernel (0: none for this band)
     int split = 0;              // one launch per length class, variant cls_var[c]
     int8_t cls_var[N_CLASSES] = {VAR_16, VAR_16, VAR_16, VAR_16};
     int32_t wide_w = 0;         // > 0: pairs wider than the warp kernel exist
@@ -86,7 +91,7 @@ struct LaunchPlan {
     PlanKey key() const {
         return {plain, C, C16 * lane16, regs_high, sort, fast, wide_w, warp_blocks, split,
                 split ? cls_var[0] | (cls_var[1] << 4) | (cls_var[2] << 8) | (cls_var[3] << 12) : 0,
-                split ? 1 : groupk, 0};
+                split ? 1 : groupk, split ? 0 : half};
     }
 };
 
@@ -122,6 +127,7 @@ int pick_slots_per_lane(int32_t w);
 int pick_slots16(int32_t w);
 int warp_occupancy(int C);
 int warp16_occupancy(int C, int high);
+int warp16h_occupancy(int C16);   // two pairs per warp; 0 where none exists
 int warp16k_occupancy(int C16, int K);
 
 int slot_init(agatha_ctx *ctx, Ledger &ledger, Slot *s);

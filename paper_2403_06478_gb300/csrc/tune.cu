@@ -83,12 +83,14 @@ LaunchPlan single_variant(LaunchPlan vp, int variant) {
     vp.lane16 = variant != VAR_32;
     vp.regs_high = variant == VAR_16_HIGHREG;
     vp.groupk = variant_warps(variant);
+    vp.half = variant == VAR_16_HALF;
     return vp;
 }
 
 // Whether this plan can run a variant (the 2- and 4-warp kernels exist for
-// the 16- and 24-slot bands only).
+// the 16- and 24-slot bands only, two pairs per warp for the 4-slot band).
 bool variant_available(const LaunchPlan &lp, int v) {
+    if (v == VAR_16_HALF) return lp.warp16h_blocks > 0;
     const int K = variant_warps(v);
     return K == 1 || lp.warp16k_blocks[K == 4] > 0;
 }
@@ -219,7 +221,7 @@ void tune_load(agatha_ctx *ctx) {
 int tune_apply(agatha_ctx *ctx, const agatha_batch *batch, const DevParams &p, uint32_t flags,
                cudaStream_t s, LaunchPlan *lp) {
     const uint32_t off = AGATHA_NO_TUNE | AGATHA_PLAIN | AGATHA_FORCE32 | AGATHA_NO_SORT | AGATHA_REGS_HIGH |
-                         AGATHA_WARPS2 | AGATHA_WARPS4;
+                         AGATHA_WARPS2 | AGATHA_WARPS4 | AGATHA_HALF_WARP;
     if (!ctx->autotune || (flags & off) || lp->plain || !lp->lane16 || !lp->sort) return AGATHA_OK;
     const std::string key = tune_key(ctx, p, lp->C16);
     TuneChoice choice;
@@ -245,6 +247,7 @@ int tune_apply(agatha_ctx *ctx, const agatha_batch *batch, const DevParams &p, u
         lp->lane16 = v != VAR_32;
         lp->regs_high = v == VAR_16_HIGHREG;
         lp->groupk = variant_warps(v);
+        lp->half = v == VAR_16_HALF;
         return AGATHA_OK;
     }
     for (int c = 0; c < N_CLASSES; ++c)

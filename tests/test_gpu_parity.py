@@ -25,6 +25,7 @@ PATHS = {
     "force32_edge": A.AGATHA_FORCE32 | A.AGATHA_EDGE_PATH_ONLY,
     "regs_high": A.AGATHA_REGS_HIGH,
     "regs_high_edge": A.AGATHA_REGS_HIGH | A.AGATHA_EDGE_PATH_ONLY,
+    "half_warp": A.AGATHA_HALF_WARP,            # two pairs per warp (bands up to 127)
 }
 
 
@@ -96,7 +97,10 @@ def test_adversarial_pairs(ctx, si):
     scoring = ADVERSARIAL_SCORINGS[si]
     batch = _adversarial_batch(np.random.default_rng(100 + si), scoring)
     ref = O.align_batch(batch)
-    for path in ("batched", "plain", "edge_only", "force32", "regs_high"):
+    paths = ["batched", "plain", "edge_only", "force32", "regs_high"]
+    if 0 < scoring.w <= 127:                    # the band two pairs per warp take
+        paths.append("half_warp")
+    for path in paths:
         got = A.agatha_align_batch(ctx, batch, flags=PATHS[path])
         _assert_same(got, ref, batch, f"adversarial[{si}]/{path}")
 
@@ -211,7 +215,7 @@ def test_short_reads_with_bwa_parameters(ctx):
     # end bonus 5): every pair of a 3,000-pair slice, batched and plain
     batch = W.make_config("short", n_pairs=3000)
     ref = O.align_batch(batch)
-    for path in ("batched", "plain", "force32"):
+    for path in ("batched", "plain", "force32", "half_warp"):
         _assert_same(A.agatha_align_batch(ctx, batch, flags=PATHS[path]), ref, batch, f"short/{path}")
     assert ref["reach_end"].sum() > 0          # the end bonus takes effect
 
@@ -332,3 +336,36 @@ def test_warps_per_pair_rejects_other_bands(ctx):
     with pytest.raises(A.AgathaError) as e:
         A.agatha_align_batch(ctx, batch, flags=A.AGATHA_WARPS2)
     assert e.value.code == A.AGATHA_ENOTSUP
+
+
+def test_half_warp_rejects_wider_bands(ctx):
+    batch = W.make_config("ont", n_pairs=8)            # w = 500: 16-slot frame
+    with pytest.raises(A.AgathaError) as e:
+        A.agatha_align_batch(ctx, batch, flags=A.AGATHA_HALF_WARP)
+    assert e.value.code == A.AGATHA_ENOTSUP
+    with pytest.raises(A.AgathaError) as e:
+        A.agatha_align_batch(ctx, W.make_config("small", n_pairs=8),
+                             flags=A.AGATHA_HALF_WARP | A.AGATHA_WARPS2)
+    assert e.value.code == A.AGATHA_EINVAL
+
+
+def test_half_warp_pairs_of_uneven_lengths(ctx):
+    # two pairs per warp whose lengths, stops and overflows differ: each half
+    # warp takes its own pairs and goes its own way through the steps
+    rng = np.random.default_rng(23)
+    scoring = W.Scoring(2, 4, 4, 2, 24, 1, 60, 40, 3)
+    qs, ts = [], []
+    for k in range(600):
+        L = int(rng.integers(0, 400))
+        q = rng.integers(0, 4, L).astype(np.uint8)
+        if k % 3 == 0:
+            t = q.copy()
+        elif k % 3 == 1:
+            t = rng.integers(0, 4, max(0, L + int(rng.integers(-70, 70)))).astype(np.uint8)
+        else:
+            t = np.concatenate([q[: L // 3], rng.integers(0, 4, L - L // 3)]).astype(np.uint8)
+        qs.append(q); ts.append(t)
+    batch = W.from_pairs(qs, ts, scoring, name="uneven")
+    ref = O.align_batch(batch)
+    for flags in (A.AGATHA_HALF_WARP, A.AGATHA_HALF_WARP | A.AGATHA_NO_SORT):
+        _assert_same(A.agatha_align_batch(ctx, batch, flags=flags), ref, batch, f"uneven/{flags}")

@@ -99,3 +99,30 @@ def test_malformed_cache_lines_are_ignored(tmp_path, batch):
                     + _key(batch.scoring, 16) + " 0 1 2 0 7\n")
     with A.Context(0, autotune=True, tune_cache_path=str(path)) as ctx:
         assert ctx.tune_variants(batch.scoring) is None
+
+
+@pytest.fixture(scope="module")
+def short_batch():
+    B.build()
+    return W.make_config("short", n_pairs=4000)
+
+
+@pytest.mark.parametrize("variants,split", [((5, 5, 5, 5), 0), ((5, 1, 0, 5), 1), ((1, 5, 2, 5), 1)])
+def test_half_warp_variant_is_exact(tmp_path, short_batch, variants, split):
+    """Two pairs per warp (variant 5, the 4-slot band only), alone and beside
+    other variants per length class, against the oracle on every pair."""
+    path = tmp_path / "tune.txt"
+    path.write_text(_key(short_batch.scoring, 4) + " " + " ".join(map(str, variants)) + f" {split}\n")
+    ref = O.align_batch(short_batch)
+    with A.Context(0, autotune=True, tune_cache_path=str(path)) as ctx:
+        assert ctx.tune_variants(short_batch.scoring) == list(variants) + [split]
+        got = A.agatha_align_batch(ctx, short_batch)
+    assert A.results_equal(got, ref, O.COMPARE_FIELDS).size == 0
+
+
+def test_half_warp_variant_not_taken_for_wider_bands(tmp_path, batch, reference):
+    # a cache entry naming it for a 16-slot band falls back to the default plan
+    path = tmp_path / "tune.txt"
+    path.write_text(_key(batch.scoring, 16) + " 5 5 5 5 0\n")
+    with A.Context(0, autotune=True, tune_cache_path=str(path)) as ctx:
+        assert A.results_equal(A.agatha_align_batch(ctx, batch), reference).size == 0
