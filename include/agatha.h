@@ -341,7 +341,14 @@ typedef struct {
     int32_t max_batch_pairs;    /* pairs merged into one launch; 0: 8192   */
     int32_t linger_us;          /* hold a short head batch this long for   */
                                 /* more requests; 0: launch at once        */
-    int32_t pad;
+    uint32_t launch_flags;      /* plan of every launch: 0 = the context's */
+                                /* autotuned plan; AGATHA_WARPS2 or        */
+                                /* AGATHA_WARPS4 = 2 or 4 warps per pair   */
+                                /* (shorter latency for long pairs; a     */
+                                /* launch whose band has no such kernel    */
+                                /* runs one warp per pair), with or       */
+                                /* without AGATHA_REGS_HIGH; any other bit */
+                                /* is EINVAL                               */
 } agatha_serve_config;
 
 typedef struct {

@@ -99,7 +99,7 @@ class agatha_config(ctypes.Structure):
 class agatha_serve_config(ctypes.Structure):
     _fields_ = [("mem_budget_bytes", ctypes.c_int64), ("max_inflight", ctypes.c_int32),
                 ("max_batch_pairs", ctypes.c_int32), ("linger_us", ctypes.c_int32),
-                ("pad", ctypes.c_int32)]
+                ("launch_flags", ctypes.c_uint32)]
 
 
 class agatha_serve_stats(ctypes.Structure):
@@ -437,10 +437,10 @@ class Server:
     not be read before ``wait`` (or ``poll``) reports completion."""
 
     def __init__(self, ctx: Context, mem_budget_bytes: int = 0, max_inflight: int = 0,
-                 max_batch_pairs: int = 0, linger_us: int = 0):
+                 max_batch_pairs: int = 0, linger_us: int = 0, launch_flags: int = 0):
         self.ctx = ctx
         cfg = agatha_serve_config(int(mem_budget_bytes), int(max_inflight), int(max_batch_pairs),
-                                  int(linger_us), 0)
+                                  int(linger_us), int(launch_flags))
         _check(lib().agatha_serve_start(ctx.handle, ctypes.byref(cfg)), ctx.handle,
                "agatha_serve_start")
         self._out = {}          # ticket -> result array the library writes into

@@ -331,9 +331,17 @@ cudaError_t launch_slot(ServeState *S, ServeSlot *s, const DevParams &p, int32_t
     shape.max_w_all = std::max<int32_t>(max_w, 1);
     shape.max_w_warp = shape.max_w_all;
     LaunchPlan lp;
-    if (make_plan(ctx, p, shape, 0, &lp) != AGATHA_OK) return cudaErrorInvalidValue;
-    // the plan the context's autotuner chose for this scoring, if any (no measuring here)
-    if (tune_apply(ctx, nullptr, p, AGATHA_DEVICE_PTRS, st, &lp) != AGATHA_OK) return cudaErrorInvalidValue;
+    const uint32_t lf = S->cfg.launch_flags;
+    if (make_plan(ctx, p, shape, lf & AGATHA_REGS_HIGH, &lp) != AGATHA_OK) return cudaErrorInvalidValue;
+    if (lf) {
+        // the server's own plan: several warps per pair where the band has that
+        // kernel, one warp per pair elsewhere
+        const int K = (lf & AGATHA_WARPS4) ? 4 : ((lf & AGATHA_WARPS2) ? 2 : 1);
+        if (K > 1 && lp.lane16 && lp.warp16k_blocks[K == 4] > 0) lp.groupk = K;
+    } else {
+        // the plan the context's autotuner chose for this scoring, if any (no measuring here)
+        if (tune_apply(ctx, nullptr, p, AGATHA_DEVICE_PTRS, st, &lp) != AGATHA_OK) return cudaErrorInvalidValue;
+    }
 
     DevBatch *desc = s->slot.h_desc;
     desc->q_packed = (const uint32_t *)(d + L.q_packed);
@@ -504,8 +512,10 @@ extern "C" int agatha_serve_start(agatha_ctx *ctx, const agatha_serve_config *cf
     if (!ctx) return AGATHA_EINVAL;
     agatha_serve_config c{};
     if (cfg) c = *cfg;
+    const uint32_t plan_bits = AGATHA_WARPS2 | AGATHA_WARPS4 | AGATHA_REGS_HIGH;
     if (c.mem_budget_bytes < 0 || c.max_inflight < 0 || c.max_inflight > kMaxInflight ||
-        c.max_batch_pairs < 0 || c.linger_us < 0)
+        c.max_batch_pairs < 0 || c.linger_us < 0 || (c.launch_flags & ~plan_bits) ||
+        ((c.launch_flags & AGATHA_WARPS2) && (c.launch_flags & AGATHA_WARPS4)))
         return set_error(ctx, AGATHA_EINVAL, "bad serving config");
     if (c.mem_budget_bytes == 0) c.mem_budget_bytes = kDefaultBudget;
     if (c.max_inflight == 0) c.max_inflight = kDefaultInflight;

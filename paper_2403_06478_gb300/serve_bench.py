@@ -43,7 +43,7 @@ def _point(ctx, pool_pb, pool, rate, args, rng):
                              pool_pb.t_len[r.pair_idx]) for r in reqs]
     srv = A.Server(ctx, mem_budget_bytes=int(args.budget_gb * (1 << 30)),
                    max_inflight=args.max_inflight, max_batch_pairs=args.max_batch_pairs,
-                   linger_us=args.linger_us)
+                   linger_us=args.linger_us, launch_flags=LAUNCH_PLANS[args.plan])
     tickets = [None] * n_req
     done_at = [0.0] * n_req
     submitted = threading.Semaphore(0)
@@ -88,6 +88,12 @@ def _point(ctx, pool_pb, pool, rate, args, rng):
     }
 
 
+# launch plans the server can run: the context's autotuned plan, or several
+# warps per pair (shorter latency for the long pairs of a request)
+LAUNCH_PLANS = {"tuned": 0, "warps2": A.AGATHA_WARPS2 | A.AGATHA_REGS_HIGH,
+                "warps4": A.AGATHA_WARPS4 | A.AGATHA_REGS_HIGH}
+
+
 def main(argv=None):
     ap = argparse.ArgumentParser()
     ap.add_argument("--rates", default="10,20,50,100,200,500,1000,2000")
@@ -98,6 +104,8 @@ def main(argv=None):
     ap.add_argument("--max-inflight", type=int, default=2)
     ap.add_argument("--max-batch-pairs", type=int, default=8192)
     ap.add_argument("--linger-us", type=int, default=0)
+    ap.add_argument("--plan", default="tuned", choices=sorted(LAUNCH_PLANS),
+                    help="plan of the server's launches: the autotuned one, or 2 or 4 warps per pair")
     ap.add_argument("--device", type=int, default=0)
     ap.add_argument("--tune-cache", default=None,
                     help="autotuner cache file (the benchmark's, to serve with the same plan)")
@@ -116,6 +124,7 @@ def main(argv=None):
         line["config"] = {"workload": "serving: Poisson arrivals, 1-512 ONT-like pairs per request",
                           "budget_gb": args.budget_gb, "max_inflight": args.max_inflight,
                           "max_batch_pairs": args.max_batch_pairs, "linger_us": args.linger_us,
+                          "plan": args.plan,
                           "tuned_plan": None if tuned is None else
                           {"variants": [A.VARIANT_NAMES[v] for v in tuned[:4]], "split": bool(tuned[4])}}
         print(json.dumps(line), flush=True)

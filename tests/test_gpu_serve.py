@@ -179,3 +179,24 @@ def test_burst_runs_launches_concurrently_on_the_device(ctx, pools):
         assert A.results_equal(g, A.agatha_align_batch(ctx, b)).size == 0, f"request {i}"
     for i in (0, 11):
         assert A.results_equal(got[i], O.align_batch(reqs[i]), O.COMPARE_FIELDS).size == 0
+
+
+@pytest.mark.parametrize("flags", [A.AGATHA_WARPS2 | A.AGATHA_REGS_HIGH, A.AGATHA_WARPS4])
+def test_serving_with_several_warps_per_pair(ctx, pools, flags):
+    # the server's own plan: 2 or 4 warps per pair where the band has those
+    # kernels (ONT, HiFi: w = 500), one warp per pair elsewhere (small: w = 100)
+    reqs = _requests(pools, 40, 17)
+    got, st = _serve_all(ctx, reqs, max_inflight=2, max_batch_pairs=400, linger_us=2000,
+                         launch_flags=flags)
+    assert st["requests_done"] == len(reqs)
+    for i, (b, g) in enumerate(zip(reqs, got)):
+        assert A.results_equal(g, A.agatha_align_batch(ctx, b)).size == 0, f"request {i}"
+    ref = O.align_batch(reqs[3])
+    assert A.results_equal(got[3], ref, O.COMPARE_FIELDS).size == 0
+
+
+def test_serving_rejects_other_launch_flags(ctx):
+    for bad in (A.AGATHA_PLAIN, A.AGATHA_WARPS2 | A.AGATHA_WARPS4, A.AGATHA_HALF_WARP):
+        with pytest.raises(A.AgathaError) as e:
+            A.Server(ctx, launch_flags=bad)
+        assert e.value.code == A.AGATHA_EINVAL
