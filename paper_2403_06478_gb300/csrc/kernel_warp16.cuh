@@ -1,6 +1,7 @@
-// Batched persistent kernel on 16-bit packed lanes: one warp aligns one pair,
-// two band slots per 32-bit register, so one integer instruction updates two
-// cells of the anti-diagonal.
+// Batched persistent kernel on 16-bit packed lanes: one warp aligns one pair
+// (or 2 or 4 warps share one pair's band, or each half warp aligns its own
+// pair), two band slots per 32-bit register, so one integer instruction
+// updates two cells of the anti-diagonal.
 //
 // Frame.  Anti-diagonal r holds the band cells t in [ceil((r-w)/2),
 // floor((r+w)/2)].  This kernel numbers them by the slot j = t - B(r) with
@@ -31,15 +32,18 @@
 //     slot beyond the band can only reach the high half, which is then beyond
 //     the band as well).
 //
-// Per cell the bulk step issues about ten instructions: a bitwise mux picks
-// the substitution score from the mismatch bit (replicated by prmt), one
-// add-max and three 16x2 max form H, and each of the four gap states is one
-// add plus one 16x2 max.  Slots outside the band keep their outgoing gap
-// states at NEG through a per-slot mask, so nothing flows back into the band.
+// Per packed register (two cells) the bulk step issues: a shift and a mask of
+// the step's mismatch word and one multiply-add for the substitution, one
+// add-max, one three-input max and one max for H, one 16x2 add-max for each
+// of the four gap states, and half a three-input max for the anti-diagonal
+// maximum.  Slots outside the band keep their outgoing gap states at NEG
+// through a per-slot mask, so nothing flows back into the band.
 // The registers are updated in place: F-from-j+1 steps walk the registers
 // upwards and E-from-j-1 steps downwards, so every old value is read before it
 // is overwritten and no copies are needed.  Anti-diagonals where the band meets
-// the table's edges run the same packed update followed by per-slot masks.
+// the table's edges run the same packed update with per-slot masks (the head
+// of the table, where the virtual row and column enter, runs the bulk or the
+// tail step wherever their values follow from the recurrence itself).
 #pragma once
 
 #include <climits>
