@@ -78,6 +78,10 @@ extern "C" {
                                       16 lanes of 8 slots each (bands up to
                                       127; AGATHA_ENOTSUP for wider ones,
                                       AGATHA_EINVAL with WARPS2/WARPS4)     */
+#define AGATHA_ONE_FRAME   0x2000u /* every pair on the batch's slot frame:
+                                      without it, on a 24-slot batch, pairs
+                                      whose own band fits 640 slots take a
+                                      20-slot kernel after the main launch  */
 
 /* Flags for agatha_config.flags. */
 #define AGATHA_CFG_TIMING  0x1    /* record CUDA events around the main kernel

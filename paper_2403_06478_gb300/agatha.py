@@ -43,6 +43,7 @@ AGATHA_TB_TWO_PASS = 0x200
 AGATHA_WARPS2 = 0x400
 AGATHA_WARPS4 = 0x800
 AGATHA_HALF_WARP = 0x1000
+AGATHA_ONE_FRAME = 0x2000
 
 AGATHA_CFG_TIMING = 0x1
 AGATHA_CFG_AUTOTUNE = 0x2

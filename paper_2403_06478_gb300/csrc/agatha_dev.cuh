@@ -46,13 +46,15 @@ struct DevBatch {
     // schedule produced by the prep kernels
     int32_t *order;          // pair indices, longest predicted work first
     int32_t *counters;       // queue heads and counts (CTR_*), [3] error word
-    int32_t *wide_order;     // pairs whose band is too wide for the warp kernel
+    int32_t *wide_order;     // pairs whose band is too wide for the warp kernel, or
+                             // (narrow_w_max > 0) those the narrower frame takes
     int64_t *bucket_hist;    // scratch for the ordering
     int32_t *ovf_list;       // pairs the 16-bit kernel hands back to the 32-bit one
     const int32_t *h0;       // local extension: the initial score of each pair (else null)
     DevParams params;
     int32_t warp_w_max;      // widest band the warp kernel takes (32*C - 1)
-    int32_t pad;
+    int32_t narrow_w_max;    // > 0: pairs whose band is at most this go to the
+                             // narrow list (a frame of fewer slots per lane)
 };
 
 enum : int32_t { CTR_HEAD = 0, CTR_NWARP = 1, CTR_NWIDE = 2, CTR_ERR = 3, CTR_WIDE_HEAD = 4,
@@ -82,7 +84,7 @@ __device__ __forceinline__ void mark_step_end(int32_t *counters) {
 // Which pair list a warp kernel launch walks: the whole ordered queue, the
 // pairs the 16-bit kernel handed back, or the part of the ordered queue that
 // holds one length class (WARP_LIST_CLASS + c).
-enum : int32_t { WARP_LIST_MAIN = 0, WARP_LIST_OVERFLOW = 1, WARP_LIST_CLASS = 2 };
+enum : int32_t { WARP_LIST_NARROW = -1, WARP_LIST_MAIN = 0, WARP_LIST_OVERFLOW = 1, WARP_LIST_CLASS = 2 };
 
 // Length classes the kernel choice is tuned for, by predicted band cells:
 // class 0 >= 2^25, class 1 >= 2^23, class 2 >= 2^21, class 3 the rest.  In
@@ -245,7 +247,14 @@ struct WorkList {
 
 __device__ __forceinline__ WorkList work_list(const DevBatch &B, int32_t list) {
     WorkList L;
-    if (list == WARP_LIST_OVERFLOW) {
+    if (list == WARP_LIST_NARROW) {
+        // the pairs whose band fits the narrower frame (unordered; they are
+        // the shortest ones)
+        L.items = B.wide_order;
+        L.head = &B.counters[CTR_WIDE_HEAD];
+        L.begin = 0;
+        L.end = B.counters[CTR_NWIDE];
+    } else if (list == WARP_LIST_OVERFLOW) {
         L.items = B.ovf_list;
         L.head = &B.counters[CTR_OVF_HEAD];
         L.begin = 0;
@@ -289,6 +298,9 @@ cudaError_t launch_warp16_c(const DevBatch *d_batch, int n_blocks, cudaStream_t 
                             int list = WARP_LIST_MAIN);
 template <int C, int MINB, int G = 32>
 int occupancy_warp16_c();
+template <int C, int MINB>
+cudaError_t launch_warp16_prio(const DevBatch *d_batch, int n_blocks, cudaStream_t s, int use_fast, int list,
+                               int priority);
 // K warps share one pair's band (C slots per lane of each warp).
 template <int C, int K, int MINB>
 cudaError_t launch_warp16k_c(const DevBatch *d_batch, int n_blocks, cudaStream_t s, int use_fast, int list);

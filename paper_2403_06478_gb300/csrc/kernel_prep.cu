@@ -38,7 +38,9 @@ __global__ void prep_classify_kernel(const DevBatch *__restrict__ d_batch, int32
         }
         const int32_t tl = B.t_len[i], ql = B.q_len[i];
         const int32_t w = effective_w(B.params.w, tl, ql);
-        if (w > B.warp_w_max) {
+        if (w > B.warp_w_max || (B.narrow_w_max > 0 && w <= B.narrow_w_max)) {
+            // too wide for the warp kernel (the block kernel's list), or a band
+            // the narrower frame takes (its own list; never both in one batch)
             const int32_t k = atomicAdd(&B.counters[CTR_NWIDE], 1);
             B.wide_order[k] = (int32_t)i;
             continue;
@@ -74,7 +76,7 @@ __global__ void prep_scatter_kernel(const DevBatch *__restrict__ d_batch) {
         if (!pair_valid(B, i)) continue;
         const int32_t tl = B.t_len[i], ql = B.q_len[i];
         const int32_t w = effective_w(B.params.w, tl, ql);
-        if (w > B.warp_w_max) continue;
+        if (w > B.warp_w_max || (B.narrow_w_max > 0 && w <= B.narrow_w_max)) continue;
         const int32_t b = work_bucket(tl, ql, w);
         const int64_t pos = (int64_t)atomicAdd((unsigned long long *)&B.bucket_hist[b], 1ull);
         B.order[pos] = (int32_t)i;

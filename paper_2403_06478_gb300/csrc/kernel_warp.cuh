@@ -424,7 +424,8 @@ struct WarpPair {
 // Pairs the warp kernel takes: valid and narrow enough for 32*C slots.
 __device__ __forceinline__ bool warp_takes(const DevBatch &B, int32_t pair) {
     const int32_t tl = B.t_len[pair], ql = B.q_len[pair];
-    return effective_w(B.params.w, tl, ql) <= B.warp_w_max;
+    const int32_t w = effective_w(B.params.w, tl, ql);
+    return w <= B.warp_w_max && (B.narrow_w_max <= 0 || w > B.narrow_w_max);
 }
 
 template <int C>

@@ -135,8 +135,8 @@ struct Xchg16 {
 template <int C, bool DMREG, bool DEFER = false, bool DIR = false, bool SCORE = !DIR, int K = 1,
           bool FHEAD = false, bool EDEFER = false, int G = 32>
 struct WarpPair16 {
-    static_assert(C == 4 || C == 6 || C == 8 || C == 12 || C == 16 || C == 24,
-                  "16-bit lanes use 4, 6, 8, 12, 16 or 24 slots per lane");
+    static_assert(C == 4 || C == 6 || C == 8 || C == 12 || C == 16 || C == 20 || C == 24,
+                  "16-bit lanes use 4, 6, 8, 12, 16, 20 or 24 slots per lane");
     static_assert(K == 1 || K == 2 || K == 4, "1, 2 or 4 warps per pair");
     static_assert(K == 1 || !DIR, "the traceback variants run one warp per pair");
     static_assert(G == 32 || (G == 16 && K == 1 && !DIR), "half-warp pairs: one group, score only");
@@ -352,6 +352,12 @@ struct WarpPair16 {
         else if constexpr (C == 8) return {((uint32_t)nm & 0xffu) | (((uint32_t)nm & 0xff00u) << 8), 0u};
         else if constexpr (C == 6) return {((uint32_t)nm & 0x3fu) | (((uint32_t)nm & 0xfc0u) << 10), 0u};
         else if constexpr (C == 4) return {((uint32_t)nm & 0xfu) | (((uint32_t)nm & 0xf0u) << 12), 0u};
+        else if constexpr (C == 20) {
+            // slots 0..9 and 10..19 (bits 0..18 and 20..38); registers 0..7
+            // in lo, 8..9 in hi
+            return {((uint32_t)nm & 0xffffu) | ((uint32_t)(nm >> 4) & 0xffff0000u),
+                    ((uint32_t)(nm >> 16) & 0xfu) | ((uint32_t)(nm >> 20) & 0xf0000u)};
+        }
         else {
             // slots 0..11 and 12..23; registers 0..7 in lo, 8..11 in hi
             const uint32_t a = (uint32_t)(nm & 0xffffffu), b = (uint32_t)(nm >> 24);
@@ -1276,8 +1282,8 @@ warp16_align_kernel(const DevBatch *__restrict__ d_batch, int32_t use_fast, int3
     const uint32_t gm = G == 32 ? FULL : 0xffffu << (threadIdx.x & 16);
     const WorkList L = work_list(B, list);
     // the larger register budget of each slot count: 4 blocks per SM for
-    // 4 slots per lane, 2 for 24, 3 otherwise
-    constexpr bool HIGH = C == 4 ? MINB == 4 : (C == 24 ? MINB == 2 : MINB == 3);
+    // 4 slots per lane, 2 for 20 and 24, 3 otherwise
+    constexpr bool HIGH = C == 4 ? MINB == 4 : ((C == 24 || C == 20) ? MINB == 2 : MINB == 3);
     using Pair = WarpPair16<C, (MINB < 4 && C <= 16) || MINB < 3, true, false, true, 1, HIGH, HIGH, G>;
     if constexpr (G == 32) {
         for (;;) {
@@ -1374,6 +1380,25 @@ cudaError_t launch_warp16_c(const DevBatch *d_batch, int n_blocks, cudaStream_t 
                             int list) {
     warp16_align_kernel<C, MINB, G><<<n_blocks, WARP_BLOCK_THREADS, 0, s>>>(d_batch, use_fast, list);
     return cudaGetLastError();
+}
+
+// The same launch at a given stream priority (lower is more urgent): the
+// 24-slot launch ahead of the 20-slot one that runs beside it, whose blocks
+// then take SMs only as the first one's blocks leave.
+template <int C, int MINB>
+cudaError_t launch_warp16_prio(const DevBatch *d_batch, int n_blocks, cudaStream_t s, int use_fast, int list,
+                               int priority) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)n_blocks);
+    cfg.blockDim = dim3(WARP_BLOCK_THREADS);
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributePriority;
+    attr[0].val.priority = priority;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, warp16_align_kernel<C, MINB, 32>, d_batch, use_fast, list);
 }
 
 template <int C, int MINB, int G>

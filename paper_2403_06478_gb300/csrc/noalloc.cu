@@ -138,7 +138,7 @@ extern "C" int agatha_align_batch_noalloc(const agatha_batch *batch, const agath
     desc.h0 = nullptr;
     desc.params = p;
     desc.warp_w_max = warp_w_max;
-    desc.pad = 0;
+    desc.narrow_w_max = 0;
     const DevBatch *d_desc = (const DevBatch *)(ds->scratch + kOffDesc);
 
     // the array keeps the previous call's contents: reset what must start at zero

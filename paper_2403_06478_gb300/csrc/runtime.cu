@@ -272,7 +272,25 @@ static cudaError_t enqueue_part(agatha_ctx *ctx, Slot *sl, const LaunchPlan &lp,
     if (lp.plain) return launch_plain_kernel(d, lp.plain_blocks, lp.plain_w, 0, s);
     bool any16 = false;
     if (!lp.split) {
-        if (lp.lane16 && lp.half) {
+        if (lp.lane16 && lp.narrow_w > 0) {
+            // the 24-slot launch and, beside it on a branch, the 20-slot one
+            // over the pairs whose band fits 640 slots (the shortest); the
+            // first at the higher priority, so that its blocks take the SMs
+            // and the second's fill them as the first's leave
+            if ((e = cudaEventRecord(sl->fork, s)) != cudaSuccess) return e;
+            if ((e = cudaStreamWaitEvent(sl->aux[0], sl->fork, 0)) != cudaSuccess) return e;
+            e = lp.regs_high ? launch_warp16_prio<24, 2>(d, lp.warp16_blocks[1], s, lp.fast, WARP_LIST_MAIN,
+                                                         ctx->prio_greatest)
+                             : launch_warp16_prio<24, 3>(d, lp.warp16_blocks[0], s, lp.fast, WARP_LIST_MAIN,
+                                                         ctx->prio_greatest);
+            if (e != cudaSuccess) return e;
+            if ((e = launch_warp16_prio<20, 2>(d, lp.narrow_blocks, sl->aux[0], lp.fast, WARP_LIST_NARROW,
+                                               ctx->prio_least)) != cudaSuccess)
+                return e;
+            if ((e = cudaEventRecord(sl->join[0], sl->aux[0])) != cudaSuccess) return e;
+            if ((e = cudaStreamWaitEvent(s, sl->join[0], 0)) != cudaSuccess) return e;
+            any16 = true;
+        } else if (lp.lane16 && lp.half) {
             e = launch_warp16h(lp.C16, d, lp.warp16h_blocks, s, lp.fast, WARP_LIST_MAIN);
             any16 = true;
         } else if (lp.lane16 && lp.groupk > 1) {
@@ -491,6 +509,22 @@ int make_plan(agatha_ctx *ctx, const DevParams &p, const BatchShape &shape, uint
     return AGATHA_OK;
 }
 
+// Frame per pair: on a single launch of the 24-slot 16-bit kernel with one
+// warp per pair over the ordered queue, the pairs whose own band fits a
+// 640-slot frame (w_eff <= 638) take the 20-slot kernel instead, after it
+// (AGATHA_ONE_FRAME keeps every pair on the batch's frame).
+void apply_narrow(agatha_ctx *ctx, LaunchPlan *lp, uint32_t flags) {
+    lp->narrow_w = 0;
+    lp->narrow_blocks = 0;
+    if ((flags & AGATHA_ONE_FRAME) || !lp->lane16 || lp->plain || !lp->sort || lp->split || lp->groupk != 1 ||
+        lp->half || lp->wide_w || lp->C16 != 24)
+        return;
+    const int occ = occupancy_warp16_c<20, 2>();
+    if (occ <= 0) return;
+    lp->narrow_w = 32 * 20 - 2;
+    lp->narrow_blocks = ctx->n_sm * occ;
+}
+
 void fill_desc(const Slot *sl, DevBatch *d, const DevParams &p, const LaunchPlan &lp, void *order,
                void *wide_order, void *ovf_list) {
     d->order = (lp.sort && !lp.plain) ? (int32_t *)order : nullptr;
@@ -501,7 +535,7 @@ void fill_desc(const Slot *sl, DevBatch *d, const DevParams &p, const LaunchPlan
     d->h0 = nullptr;
     d->params = p;
     d->warp_w_max = lp.plain ? INT32_MAX : lp.warp_w_max;
-    d->pad = 0;
+    d->narrow_w_max = lp.plain ? 0 : lp.narrow_w;
 }
 
 }  // namespace agatha
@@ -541,6 +575,10 @@ extern "C" int agatha_init(agatha_ctx **out, const agatha_config *cfg) {
     ctx->n_sm = prop.multiProcessorCount;
     ctx->cc_major = prop.major;
     ctx->cc_minor = prop.minor;
+    if (cudaDeviceGetStreamPriorityRange(&ctx->prio_least, &ctx->prio_greatest) != cudaSuccess) {
+        cudaGetLastError();
+        ctx->prio_least = ctx->prio_greatest = 0;
+    }
     if ((e = cudaStreamCreateWithFlags(&ctx->stream, cudaStreamNonBlocking)) != cudaSuccess) {
         delete ctx;
         return AGATHA_ECUDA;
@@ -716,6 +754,7 @@ extern "C" int agatha_align_batch(agatha_ctx *ctx, const agatha_batch *batch,
         lp.wide_w = plain_kernel_max_w();
     }
     if ((rc = tune_apply(ctx, batch, p, flags, s, &lp))) return rc;
+    apply_narrow(ctx, &lp, flags);
     rc = run_planned(ctx, batch, p, out, flags, s, lp, ctx->timing ? ctx->ev_k0 : nullptr,
                      ctx->timing ? ctx->ev_k1 : nullptr);
     if (rc == AGATHA_OK) ctx->timed_once = true;

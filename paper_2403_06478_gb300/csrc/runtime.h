@@ -83,6 +83,9 @@ struct LaunchPlan {
     int warp16k_blocks[2] = {0, 0};  // grids of the 2- and 4-warp kernels (0: none)
     int half = 0;               // the single launch runs two pairs per warp
     int warp16h_blocks = 0;     // grid of that kernel (0: none for this band)
+    int32_t narrow_w = 0;       // > 0: pairs whose band is at most this run on
+                                // the 20-slot frame, beside the 24-slot launch
+    int narrow_blocks = 0;      // grid of that kernel
     int split = 0;              // one launch per length class, variant cls_var[c]
     int8_t cls_var[N_CLASSES] = {VAR_16, VAR_16, VAR_16, VAR_16};
     int32_t wide_w = 0;         // > 0: pairs wider than the warp kernel exist
@@ -91,7 +94,7 @@ struct LaunchPlan {
     PlanKey key() const {
         return {plain, C, C16 * lane16, regs_high, sort, fast, wide_w, warp_blocks, split,
                 split ? cls_var[0] | (cls_var[1] << 4) | (cls_var[2] << 8) | (cls_var[3] << 12) : 0,
-                split ? 1 : groupk, split ? 0 : half};
+                split ? 1 : groupk, (split ? 0 : half) | (narrow_w > 0 ? 2 : 0)};
     }
 };
 
@@ -128,6 +131,7 @@ int pick_slots16(int32_t w);
 int warp_occupancy(int C);
 int warp16_occupancy(int C, int high);
 int warp16h_occupancy(int C16);   // two pairs per warp; 0 where none exists
+void apply_narrow(agatha_ctx *ctx, LaunchPlan *lp, uint32_t flags);
 int warp16k_occupancy(int C16, int K);
 
 int slot_init(agatha_ctx *ctx, Ledger &ledger, Slot *s);
@@ -171,6 +175,7 @@ struct agatha_ctx {
     int device = 0;
     int n_sm = 0;
     int cc_major = 0, cc_minor = 0;
+    int prio_least = 0, prio_greatest = 0;   // the device's stream priority range
     cudaStream_t stream = nullptr;
     agatha::Ledger ledger;
     std::string tune_cache_path;

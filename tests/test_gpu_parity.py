@@ -26,6 +26,7 @@ PATHS = {
     "regs_high": A.AGATHA_REGS_HIGH,
     "regs_high_edge": A.AGATHA_REGS_HIGH | A.AGATHA_EDGE_PATH_ONLY,
     "half_warp": A.AGATHA_HALF_WARP,            # two pairs per warp (bands up to 127)
+    "one_frame": A.AGATHA_ONE_FRAME,            # no narrower frame for short pairs
 }
 
 
@@ -97,7 +98,7 @@ def test_adversarial_pairs(ctx, si):
     scoring = ADVERSARIAL_SCORINGS[si]
     batch = _adversarial_batch(np.random.default_rng(100 + si), scoring)
     ref = O.align_batch(batch)
-    paths = ["batched", "plain", "edge_only", "force32", "regs_high"]
+    paths = ["batched", "plain", "edge_only", "force32", "regs_high", "one_frame"]
     if 0 < scoring.w <= 127:                    # the band two pairs per warp take
         paths.append("half_warp")
     for path in paths:
@@ -369,3 +370,24 @@ def test_half_warp_pairs_of_uneven_lengths(ctx):
     ref = O.align_batch(batch)
     for flags in (A.AGATHA_HALF_WARP, A.AGATHA_HALF_WARP | A.AGATHA_NO_SORT):
         _assert_same(A.agatha_align_batch(ctx, batch, flags=flags), ref, batch, f"uneven/{flags}")
+
+
+def test_short_pairs_of_a_wide_band_on_the_narrower_frame(ctx):
+    # a 24-slot batch (w = 750): pairs whose own band fits 640 slots run on
+    # the 20-slot kernel after the main launch; with AGATHA_ONE_FRAME all run
+    # on the 24-slot one.  Both against the oracle on every pair, with lengths
+    # on both sides of the 638 boundary.
+    rng = np.random.default_rng(31)
+    sk = W.make_config("skewed", n_pairs=2500)
+    qs = [sk.query(i) for i in range(sk.n_pairs)]
+    ts = [sk.target(i) for i in range(sk.n_pairs)]
+    for L in (1, 60, 400, 636, 637, 638, 639, 640, 700):
+        q = rng.integers(0, 4, L).astype(np.uint8)
+        qs += [q, q]
+        ts += [q.copy(), rng.integers(0, 4, max(1, L + int(rng.integers(-3, 4)))).astype(np.uint8)]
+    batch = W.from_pairs(qs, ts, sk.scoring, name="narrow")
+    weff = np.minimum(np.maximum(batch.t_len, batch.q_len), sk.scoring.w)
+    assert (weff <= 638).sum() > 100 and (weff > 638).sum() > 100
+    ref = O.align_batch(batch)
+    for flags in (0, A.AGATHA_ONE_FRAME, A.AGATHA_REGS_HIGH):
+        _assert_same(A.agatha_align_batch(ctx, batch, flags=flags), ref, batch, f"narrow/{flags}")
